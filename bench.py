@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark of the w-product hot path on GB300.
+
+Workload ("hsi-256x256x192-L3"): two synthetic hyperspectral-shaped cubes
+A, B in R^{256x256x192} (rank-20 products of Gaussian factors with smooth
+spectral tubes plus 1% noise, min-max normalised; seeds 0 and 1), L = 3.
+One step = one pass of the hot path over that input:
+    C   = A *w B               (mixed-precision face-products, default bf16x3)
+    C_r = rank-20 w-svd of A   (when the library provides it)
+    C_s = rank-20 sp-w-svd of A
+`value` is the w-product throughput in TFLOP/s counting the algorithmic
+2 n1 n2 n4 p flops once; the w-svd / sp-w-svd times are reported beside it,
+and the same w-product in plain FP32 is timed in a second loop for the
+mixed-vs-FP32 comparison, with both errors against the FP64 oracle.
+
+Protocol: inputs resident in HBM; W >= 3 untimed warm-up steps; a 512 MiB
+buffer is written between timed steps to flush the 129 MB L2; every timed
+interval is a pair of CUDA events on the launching stream; per-kernel times
+come from the library's own event profiler (wp_profile_*).  SM clocks are
+sampled with nvidia-smi during the timed loop.  Under torchrun every rank runs
+its own independent replica (weak scaling); the time is the max over ranks.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="hsi-256x256x192-L3", n1=256, n2=256, n4=256, p=192, L=3, r=20)
+METRIC = "w-product TFLOP/s & w-svd ms at 256x256x192; mixed vs FP32 at <=1e-5 rel err"
+FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", default="bf16x3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def inputs(np_dtype=np.float32):
+    from paper_2601_08228_gb300 import synth
+    w = WORKLOAD
+    A = synth.hsi_cube(w["n1"], w["n2"], w["p"], seed=0, dtype=np_dtype)
+    B = synth.hsi_cube(w["n2"], w["n4"], w["p"], seed=1, dtype=np_dtype)
+    return A, B
+
+
+def wprod_flops():
+    w = WORKLOAD
+    return 2.0 * w["n1"] * w["n2"] * w["n4"] * w["p"]
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- peaks / roofline
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d["bf16_tflops_sustained"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0,
+            "source": "fallback"}
+
+
+def fp32_simt_peak_tflops(sm_count, mhz):
+    """2 flops (FMA) x 128 FP32 lanes per SM x SMs x clock."""
+    return 2.0 * 128 * sm_count * mhz * 1e6 / 1e12
+
+
+def _src_hash(fname):
+    path = os.path.join(ROOT, "paper_2601_08228_gb300", "csrc", fname)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] if os.path.exists(path) else None
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when it is absent or the kernel's source changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d or _src_hash(d.get("source", "")) != d.get("source_sha"):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    import oracle as O
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    A, B = inputs(np.float64)
+    w = WORKLOAD
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.wprod(A, B, w["L"])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = wprod_flops() * args.steps / tot / 1e12
+    cores = _blas_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["workload"], "L": w["L"], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": "FP64 NumPy oracle w-product on the full 256x256x192 workload, per step"},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def cpu_baseline_sample():
+    """Oracle w-product on the bench workload (FP64), bounded to ~10-20 s."""
+    import oracle as O
+    A, B = inputs(np.float64)
+    L = WORKLOAD["L"]
+    O.wprod(A, B, L)
+    reps, t0 = 0, time.perf_counter()
+    while reps < 30 and time.perf_counter() - t0 < 10.0:
+        O.wprod(A, B, L)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": wprod_flops() / dt / 1e12, "unit": "TFLOP/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle w-product on the full 256x256x192 workload, {reps} reps"}
+
+
+# ---------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import oracle as O
+    from paper_2601_08228_gb300 import capi
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    capi.lib()
+    w = WORKLOAD
+    L, r = w["L"], w["r"]
+    A_h, B_h = inputs(np.float32)
+    A = torch.from_numpy(A_h).cuda()
+    B = torch.from_numpy(B_h).cuda()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    prec = args.prec
+    try:
+        capi.wp_wprod(A, B, L, prec=prec)
+    except capi.WPError as e:
+        if e.status != 12:
+            raise
+        prec = "fp32"
+    have_wsvd = True
+    try:
+        capi.wp_wsvd(A, L, r)
+    except capi.WPError as e:
+        if e.status != 12:
+            raise
+        have_wsvd = False
+    torch.cuda.synchronize()
+
+    C = torch.empty((w["p"], w["n1"], w["n4"]), dtype=torch.float32, device="cuda")
+    ws_prod = torch.empty(capi.wp_wprod_workspace(w["n1"], w["n2"], w["n4"], w["p"], L, prec), dtype=torch.uint8,
+                          device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev):
+        ev[0].record(stream)
+        capi.wp_wprod(A, B, L, prec=prec, out=C, ws=ws_prod)
+        ev[1].record(stream)
+        if have_wsvd:
+            capi.wp_wsvd(A, L, r)
+            ev[2].record(stream)
+            capi.wp_wsvd(A, L, r, sparse=True)
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches0 = capi.wp_launch_count()
+    with ClockSampler(local) as clk:
+        capi.wp_profile_begin()
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            step(events[i])
+        torch.cuda.synchronize()
+        prof = capi.wp_profile_end()
+    launches = capi.wp_launch_count() - launches0
+    t_prod = sum(e[0].elapsed_time(e[1]) for e in events) / 1e3
+    t_wsvd = sum(e[1].elapsed_time(e[2]) for e in events) / 1e3 if have_wsvd else 0.0
+    t_sp = sum(e[2].elapsed_time(e[3]) for e in events) / 1e3 if have_wsvd else 0.0
+    t_step = t_prod + t_wsvd + t_sp
+    if ws > 1:
+        tt = torch.tensor([t_prod, t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_prod, t_step = tt.tolist()
+    value = ws * args.steps * wprod_flops() / t_prod / 1e12
+
+    # FP32 comparison loop (same protocol), and errors against the oracle
+    fp32 = _time_loop(lambda: capi.wp_wprod(A, B, L, prec="fp32", out=C, ws=_ws(capi, w, L, "fp32")), flush,
+                      args.warmup, args.steps)
+    C_mixed = capi.wp_wprod(A, B, L, prec=prec).cpu().numpy()
+    C_fp32 = capi.wp_wprod(A, B, L, prec="fp32").cpu().numpy()
+
+    # e2e through the public call with host buffers: H2D inputs, w-product, D2H result
+    e2e = _e2e(capi, A_h, B_h, L, prec, args.warmup, args.steps)
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    Cref = O.wprod(A_h, B_h, L)
+    err_mixed = O.rel_fro(C_mixed, Cref)
+    err_fp32 = O.rel_fro(C_fp32, Cref)
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = _roofline(prof, peaks, sm, args.steps, have_wsvd)
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3",
+                                                          "fp8": "fp8e4m3"}[prec],
+        "data": "synthetic",
+        "config": {"workload": w["workload"], "n1": w["n1"], "n2": w["n2"], "n4": w["n4"], "p": w["p"],
+                   "L": w["L"], "rank": r, "prec": prec, "l2": "flushed between steps (512 MiB write)"},
+        "parts_ms": {"wprod": 1e3 * t_prod / args.steps, "wsvd": 1e3 * t_wsvd / args.steps if have_wsvd else None,
+                     "spwsvd": 1e3 * t_sp / args.steps if have_wsvd else None},
+        "wsvd_ms": 1e3 * t_wsvd / args.steps if have_wsvd else None,
+        "fp32_tflops": args.steps * wprod_flops() / fp32 / 1e12,
+        "rel_err": {"mixed": err_mixed, "fp32": err_fp32},
+        "roofline": roof,
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+_WS_CACHE = {}
+
+
+def _ws(capi, w, L, prec):
+    import torch
+    key = (L, prec)
+    if key not in _WS_CACHE:
+        _WS_CACHE[key] = torch.empty(capi.wp_wprod_workspace(w["n1"], w["n2"], w["n4"], w["p"], L, prec),
+                                     dtype=torch.uint8, device="cuda")
+    return _WS_CACHE[key]
+
+
+def _time_loop(fn, flush, warmup, steps):
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b) / 1e3
+    return total
+
+
+def _e2e(capi, A_h, B_h, L, prec, warmup, steps):
+    import torch
+    w = WORKLOAD
+    Ap = torch.from_numpy(A_h).pin_memory()
+    Bp = torch.from_numpy(B_h).pin_memory()
+    Cp = torch.empty((w["p"], w["n1"], w["n4"]), dtype=torch.float32).pin_memory()
+    Ad, Bd = torch.empty_like(Ap, device="cuda"), torch.empty_like(Bp, device="cuda")
+    Cd = torch.empty_like(Cp, device="cuda")
+    wsb = _ws(capi, w, L, prec)
+
+    def one():
+        Ad.copy_(Ap, non_blocking=True)
+        Bd.copy_(Bp, non_blocking=True)
+        capi.wp_wprod(Ad, Bd, L, prec=prec, out=Cd, ws=wsb)
+        Cp.copy_(Cd, non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        one()
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    return {"value": steps * wprod_flops() / t / 1e12, "unit": "TFLOP/s",
+            "h2d_bytes_per_step": Ap.numel() * 4 + Bp.numel() * 4, "d2h_bytes_per_step": Cp.numel() * 4}
+
+
+def _roofline(prof, peaks, sm_count, steps, have_wsvd):
+    """Roofline entry for the kernel with the largest share of the step."""
+    if not prof:
+        return None
+    w = WORKLOAD
+    name, (launches, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / launches / 1e3
+    plane_a, plane_b, plane_c = w["n1"] * w["n2"], w["n2"] * w["n4"], w["n1"] * w["n4"]
+    if name.startswith("lift"):
+        # bytes per step of that kernel / launches per step; each element read + written once
+        per_step_elems = {"lift_forward": plane_a + plane_b + (3 * plane_a if have_wsvd else 0),
+                          "lift_inverse": plane_c + (2 * plane_a if have_wsvd else 0)}.get(name, plane_a)
+        bytes_per_launch = 8.0 * w["p"] * per_step_elems / (launches / steps)
+        ach = bytes_per_launch / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu_traffic(name), "peak_source": peaks["source"] + " hbm_gbs"}
+    if name.startswith("sgemm"):
+        flops = wprod_flops()
+        ach = flops / avg_s / 1e12
+        peak = fp32_simt_peak_tflops(sm_count, peaks["sm_max_mhz"])
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": ncu_traffic(name),
+                "peak_source": f"FP32 SIMT 2*128*{sm_count} SMs*{peaks['sm_max_mhz']:.0f} MHz"}
+    if name.startswith("tc_gemm"):
+        flops = wprod_flops()
+        ach = flops / avg_s / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": ncu_traffic(name), "peak_source": peaks["source"] + " bf16 sustained"}
+    return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": ncu_traffic(name), "avg_launch_ms": avg_s * 1e3}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * wprod.h -- C ABI of libwprod.so, the GB300 (sm_103a) w-product library.
+ *
+ * Implements the hot path of "Second-Generation Wavelet-inspired Tensor
+ * Product with Applications in Hyperspectral Imaging" (arXiv 2601.08228):
+ * the L-level lazy-Haar lifting transform along mode 3 (Sec. II-A, Eq. 1-3),
+ * the facewise products of the wavelet-domain frontal slices (Def. 2.1,
+ * Algorithm 1), facewise truncated SVDs (Algorithm 2, Thm 2.5, sp-w-svd of
+ * Sec. IV-B), the Moore-Penrose inverse (Def. 2.6, Thm 2.6), the backward
+ * pass of the w-product and a batched launch over many uneven tensors.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Tensors.  A third-order tensor A in R^{n1 x n2 x p} is a contiguous float32
+ *   array in DEVICE memory, slice-major: shape (p, n1, n2), row-major, so the
+ *   frontal slice A(:, :, k) is the dense n1 x n2 row-major matrix at offset
+ *   (k-1) * n1 * n2.  Tube length p must be a multiple of 2^L (p = 2^L m,
+ *   Sec. II-A); L = 0 is accepted and makes the w-product a plain batched
+ *   matrix product.
+ * Wavelet domain.  Transformed tensors use the Mallat coefficient order of
+ *   Eq. (1) along mode 3: slices [0, m) hold s_L, [m, 2m) hold d_L, and
+ *   [p / 2^j, p / 2^(j-1)) hold d_j.
+ * Lifting convention.  Algorithm 1 with 1-based tube positions:
+ *   d_j[k] = s_{j-1}[2k-1] - s_{j-1}[2k],  s_j[k] = s_{j-1}[2k] + d_j[k] / 2.
+ * Ownership.  The caller owns every buffer.  Work buffers are passed in as
+ *   `ws` / `ws_bytes` (device memory, 256-byte aligned); query the size with
+ *   the matching *_workspace() call.  The library never allocates device
+ *   memory on these paths.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every call only enqueues work on it and returns; no call
+ *   synchronises unless stated.
+ * Aliasing.  Outputs must not overlap inputs (WP_ERR_ALIAS).
+ * Alignment.  Every tensor pointer must be 16-byte aligned (WP_ERR_ALIGN).
+ * Errors.  Arguments are validated on the host before anything is launched;
+ *   a failing call launches nothing and returns a wp_status code.  Faults
+ *   detected inside kernels (an expired bounded wait, a Jacobi sweep limit)
+ *   are recorded in a per-device status word that wp_get_device_error()
+ *   returns and clears.  Nothing calls abort() and no kernel traps.
+ */
+#ifndef WPROD_H
+#define WPROD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WP_API __attribute__((visibility("default")))
+#else
+#define WP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WP_OK = 0,
+  WP_ERR_NULL = 1,          /* a required pointer is NULL                      */
+  WP_ERR_SHAPE = 2,         /* a dimension is < 1 or too large                 */
+  WP_ERR_LEVELS = 3,        /* L < 0, L > WP_MAX_LEVELS or p % 2^L != 0        */
+  WP_ERR_RANK = 4,          /* r < 1 or r > min(rows, cols)                    */
+  WP_ERR_PREC = 5,          /* unknown precision mode                          */
+  WP_ERR_ALIGN = 6,         /* a pointer is not 16-byte aligned                */
+  WP_ERR_WORKSPACE = 7,     /* ws is NULL or ws_bytes too small                */
+  WP_ERR_NOT_CONVERGED = 8, /* Jacobi SVD hit its sweep limit (device word)    */
+  WP_ERR_TIMEOUT = 9,       /* a bounded device-side wait expired (device word)*/
+  WP_ERR_CUDA = 10,         /* a CUDA runtime call failed                      */
+  WP_ERR_ALIAS = 11,        /* an output overlaps an input                     */
+  WP_ERR_UNSUPPORTED = 12   /* valid request this build does not implement     */
+} wp_status;
+
+/* Facewise-product arithmetic (Sec. "precision" of the library):
+ *  FP32      plain FP32 SIMT products (the reference path of the library)
+ *  BF16      one BF16 x BF16 tcgen05 product per slice, FP32 accumulation
+ *  BF16X3    split precision: x = hi + lo with hi, lo BF16; computes
+ *            hi*hi + hi*lo + lo*hi on tcgen05 tensor cores, FP32 accumulation
+ *  FP8       E4M3 operands scaled per wavelet-domain slice, tcgen05, FP32
+ *            accumulation, scales folded into the epilogue                  */
+typedef enum { WP_PREC_FP32 = 0, WP_PREC_BF16 = 1, WP_PREC_BF16X3 = 2, WP_PREC_FP8 = 3 } wp_prec;
+
+#define WP_MAX_LEVELS 10
+
+/* Human-readable name of a wp_status value (static string, never NULL). */
+WP_API const char* wp_status_string(int status);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+WP_API int wp_version(void);
+
+/* Number of kernels this library has launched in the calling process so far
+ * (a host-side counter incremented at every launch site). */
+WP_API uint64_t wp_launch_count(void);
+
+/* Per-kernel timing.  wp_profile_begin() clears the table and enables it:
+ * from then on every kernel launch is bracketed by two CUDA events recorded
+ * on the stream it is launched on.  wp_profile_end() disables recording,
+ * synchronises the device and totals the elapsed times per kernel name;
+ * wp_profile_count() / wp_profile_get() read the totals (name copied into
+ * `name`, NUL-terminated, at most name_len bytes).  Do not enable it while a
+ * stream is being captured into a CUDA graph. */
+WP_API int wp_profile_begin(void);
+WP_API int wp_profile_end(void);
+WP_API int wp_profile_count(void);
+WP_API int wp_profile_get(int index, char* name, int name_len, int64_t* launches,
+                          double* total_ms);
+
+/* Synchronise `stream`, then return and clear the device status word of the
+ * current device (WP_OK if no kernel reported a fault since the last call).
+ * Returns WP_ERR_CUDA if the synchronisation itself fails. */
+WP_API int wp_get_device_error(void* stream);
+
+/* ---- a1 / a4: lifting along mode 3 (Sec. II-A, Eq. 1-3, Algorithm 1) ---- */
+
+/* y = W_[L](x): forward lazy-Haar lifting of every mode-3 tube, all L levels
+ * in one pass (Eq. 1, Algorithm 1 forward loop).  x, y: (p, n1, n2) device
+ * float32; y is written in Mallat order.  0 <= L <= WP_MAX_LEVELS. */
+WP_API int wp_lift_forward(const float* x, float* y, int64_t n1, int64_t n2, int64_t p, int L,
+                    void* stream);
+
+/* x = W_[L]^{-1}(y): inverse lifting (Eq. 3, Algorithm 1 inverse loop).
+ * y in Mallat order, x spatial; both (p, n1, n2). */
+WP_API int wp_lift_inverse(const float* y, float* x, int64_t n1, int64_t n2, int64_t p, int L,
+                    void* stream);
+
+/* Adjoint transforms (the transform is not orthogonal, Remark 2.1).
+ * of_inverse = 0: h = W^T g     (g Mallat order -> h spatial)
+ * of_inverse = 1: h = W^{-T} g  (g spatial -> h Mallat order)              */
+WP_API int wp_lift_adjoint(const float* g, float* h, int64_t n1, int64_t n2, int64_t p, int L,
+                    int of_inverse, void* stream);
+
+/* ---- a2: face-product Delta of wavelet-domain slices (Def. 2.1) ---------- */
+
+/* Ch[k] = op(Ah[k]) op(Bh[k]) for k = 0..p-1.  op(Ah[k]) is n1 x n2: Ah is
+ * (p, n1, n2), or (p, n2, n1) when transA.  op(Bh[k]) is n2 x n4: Bh is
+ * (p, n2, n4), or (p, n4, n2) when transB.  Ch is (p, n1, n4). */
+WP_API int wp_facewise_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int prec,
+                          size_t* bytes);
+WP_API int wp_facewise(const float* Ah, const float* Bh, float* Ch, int64_t n1, int64_t n2,
+                int64_t n4, int64_t p, int transA, int transB, int prec, void* ws,
+                size_t ws_bytes, void* stream);
+
+/* ---- a1 + a2 + a4: the w-product (Def. 2.1, Algorithm 1) ---------------- */
+
+/* C = op(A) *w op(B) = W^{-1}( W(op A) Delta W(op B) ), op as in
+ * wp_facewise; C is (p, n1, n4) spatial. */
+WP_API int wp_wprod_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
+                       size_t* bytes);
+WP_API int wp_wprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
+             int64_t p, int L, int transA, int transB, int prec, void* ws, size_t ws_bytes,
+             void* stream);
+
+/* ---- a6: backward of C = A *w B (adjoint route) ------------------------- */
+
+/* Given G = dLoss/dC (p, n1, n4), computes
+ *   G_hat = W^{-T} G,  dA = W^T (G_hat Delta B_hat^T),  dB = W^T (A_hat^T Delta G_hat)
+ * with A_hat = W(A), B_hat = W(B) recomputed (not stored by the forward).
+ * A (p, n1, n2), B (p, n2, n4); dA (p, n1, n2) and dB (p, n2, n4) may each
+ * be NULL to skip that gradient. */
+WP_API int wp_wprod_backward_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L,
+                                int prec, size_t* bytes);
+WP_API int wp_wprod_backward(const float* A, const float* B, const float* G, float* dA, float* dB,
+                      int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* ---- a3: truncated w-svd and sp-w-svd (Algorithm 2, Thm 2.5, Sec. IV-B) -- */
+
+/* C_r = rank-r w-svd of A (p, n1, n2): per wavelet-domain slice a one-sided
+ * Jacobi SVD, keep the r leading triplets, inverse-transform.  sparse = 1
+ * gives sp-w-svd: only the s_L and d_L slices (Mallat rows [0, 2m)) are
+ * truncated, the finer details d_1..d_{L-1} are set to zero.
+ * Optional factor outputs (NULL to skip): U (p, n1, r), S (p, r), V (p, n2, r)
+ * -- singular vectors as columns, singular values in descending order.  With
+ * factors_in_wavelet_domain = 1 they are the per-slice factors in Mallat
+ * order; with 0 they are mapped to the spatial domain with W^{-1} (Thm 2.5).
+ * Singular vectors are determined up to sign. */
+WP_API int wp_wsvd_workspace(int64_t n1, int64_t n2, int64_t p, int L, int r, size_t* bytes);
+WP_API int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V, int64_t n1, int64_t n2,
+            int64_t p, int L, int r, int sparse, int factors_in_wavelet_domain, void* ws,
+            size_t ws_bytes, void* stream);
+
+/* ---- a5: Moore-Penrose inverse (Def. 2.6, Thm 2.6) --------------------- */
+
+/* X = A^dagger for A (p, m, n); X is (p, n, m).  Per wavelet slice
+ * pinv = V Sigma^+ U^T from the Jacobi SVD, keeping sigma_i > rtol sigma_max
+ * (rtol < 0 selects max(m, n) * FLT_EPSILON), then `refine_iters` steps of
+ * X <- X + X (I - A X) evaluated with FP64 residual accumulation, then W^{-1}. */
+WP_API int wp_wpinv_workspace(int64_t m, int64_t n, int64_t p, int L, size_t* bytes);
+WP_API int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t p, int L, double rtol,
+             int refine_iters, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- a7: batched launch over many uneven tensors ------------------------ */
+
+/* One item: C = A *w B and C_r = rank-r w-svd of A, for A (p, n1, n2),
+ * B (p, n2, n4), C (p, n1, n4), C_r (p, n1, n2); all device pointers. */
+typedef struct {
+  const float* A;
+  const float* B;
+  float* C;
+  float* C_r;
+  int32_t n1, n2, n4, p, L, r;
+} wp_batch_item;
+
+/* `items` is a HOST array of `count` descriptors; the call copies it into
+ * the workspace (one cudaMemcpyAsync) and runs every item's w-product and
+ * rank-r w-svd in persistent launches whose work lists are built on the
+ * host.  Limits: 1 <= n1, n2, n4 <= 64 and r <= min(n1, n2). */
+WP_API int wp_batched_workspace(const wp_batch_item* items, int count, size_t* bytes);
+WP_API int wp_batched(const wp_batch_item* items, int count, void* ws, size_t ws_bytes,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WPROD_H */

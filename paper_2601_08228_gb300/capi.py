@@ -1,0 +1,269 @@
+"""ctypes binding of libwprod.so (include/wprod.h), one wrapper per entry point.
+
+Argument marshalling only: each wrapper checks that its tensors are CUDA
+float32 and contiguous, allocates outputs and the workspace with PyTorch's
+allocator, passes raw device pointers plus the current CUDA stream to the C
+function, and raises WPError on a non-zero status.  Every step of the
+computation runs in the library's kernels; there is no fallback path, and a
+missing library raises at the first call.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libwprod.so")
+_lib = None
+
+PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3}
+
+STATUS_NAMES = {
+    0: "WP_OK", 1: "WP_ERR_NULL", 2: "WP_ERR_SHAPE", 3: "WP_ERR_LEVELS", 4: "WP_ERR_RANK",
+    5: "WP_ERR_PREC", 6: "WP_ERR_ALIGN", 7: "WP_ERR_WORKSPACE", 8: "WP_ERR_NOT_CONVERGED",
+    9: "WP_ERR_TIMEOUT", 10: "WP_ERR_CUDA", 11: "WP_ERR_ALIAS", 12: "WP_ERR_UNSUPPORTED",
+}
+
+
+class WPError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {lib().wp_status_string(status).decode()}")
+
+
+class WPBatchItem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("C_r", ctypes.c_void_p), ("n1", ctypes.c_int32), ("n2", ctypes.c_int32),
+                ("n4", ctypes.c_int32), ("p", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("r", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+
+_SIGNATURES = {
+    "wp_status_string": ([_I], ctypes.c_char_p),
+    "wp_version": ([], _I),
+    "wp_launch_count": ([], ctypes.c_uint64),
+    "wp_get_device_error": ([_P], _I),
+    "wp_profile_begin": ([], _I),
+    "wp_profile_end": ([], _I),
+    "wp_profile_count": ([], _I),
+    "wp_profile_get": ([_I, ctypes.c_char_p, _I, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)], _I),
+    "wp_lift_forward": ([_P, _P, _I64, _I64, _I64, _I, _P], _I),
+    "wp_lift_inverse": ([_P, _P, _I64, _I64, _I64, _I, _P], _I),
+    "wp_lift_adjoint": ([_P, _P, _I64, _I64, _I64, _I, _I, _P], _I),
+    "wp_facewise_workspace": ([_I64, _I64, _I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_facewise": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _P, _SZ, _P], _I),
+    "wp_wprod_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_wprod": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _I, _P, _SZ, _P], _I),
+    "wp_wprod_backward_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_wprod_backward": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
+    "wp_wsvd_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_wsvd": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I, _I, _I, _I, _P, _SZ, _P], _I),
+    "wp_wpinv_workspace": ([_I64, _I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_wpinv": ([_P, _P, _I64, _I64, _I64, _I, ctypes.c_double, _I, _P, _SZ, _P], _I),
+    "wp_batched_workspace": ([ctypes.POINTER(WPBatchItem), _I, ctypes.POINTER(_SZ)], _I),
+    "wp_batched": ([ctypes.POINTER(WPBatchItem), _I, _P, _SZ, _P], _I),
+}
+
+
+def lib():
+    """Load libwprod.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing: build it with paper_2601_08228_gb300.build.build()")
+        handle = ctypes.CDLL(_LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = handle
+    return _lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise WPError(status, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _req(t, name, ndim=3):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != ndim:
+        raise ValueError(f"{name} must be a contiguous CUDA float32 tensor with {ndim} dims")
+    return t
+
+
+def _prec(prec):
+    if isinstance(prec, int):
+        return prec
+    return PREC[prec]
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+# ---- lifting ------------------------------------------------------------------
+
+def wp_lift_forward(x, L, out=None):
+    _req(x, "x")
+    p, n1, n2 = x.shape
+    y = torch.empty_like(x) if out is None else _req(out, "out")
+    _check(lib().wp_lift_forward(_ptr(x), _ptr(y), n1, n2, p, L, _stream()), "wp_lift_forward")
+    return y
+
+
+def wp_lift_inverse(y, L, out=None):
+    _req(y, "y")
+    p, n1, n2 = y.shape
+    x = torch.empty_like(y) if out is None else _req(out, "out")
+    _check(lib().wp_lift_inverse(_ptr(y), _ptr(x), n1, n2, p, L, _stream()), "wp_lift_inverse")
+    return x
+
+
+def wp_lift_adjoint(g, L, of_inverse=False, out=None):
+    _req(g, "g")
+    p, n1, n2 = g.shape
+    h = torch.empty_like(g) if out is None else _req(out, "out")
+    _check(lib().wp_lift_adjoint(_ptr(g), _ptr(h), n1, n2, p, L, int(bool(of_inverse)), _stream()),
+           "wp_lift_adjoint")
+    return h
+
+
+# ---- face-product and w-product --------------------------------------------------
+
+def _prod_dims(A, B, transA, transB):
+    p = A.shape[0]
+    n1, n2 = (A.shape[2], A.shape[1]) if transA else (A.shape[1], A.shape[2])
+    n2b, n4 = (B.shape[2], B.shape[1]) if transB else (B.shape[1], B.shape[2])
+    if B.shape[0] != p or n2b != n2:
+        raise ValueError(f"shape mismatch: op(A) {n1}x{n2}, op(B) {n2b}x{n4}")
+    return p, n1, n2, n4
+
+
+def wp_facewise(Ah, Bh, transA=False, transB=False, prec="fp32", out=None):
+    _req(Ah, "Ah"), _req(Bh, "Bh")
+    p, n1, n2, n4 = _prod_dims(Ah, Bh, transA, transB)
+    pr = _prec(prec)
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_facewise_workspace(n1, n2, n4, p, pr, ctypes.byref(nbytes)), "wp_facewise_workspace")
+    ws = _workspace(nbytes.value, Ah.device)
+    C = torch.empty((p, n1, n4), dtype=torch.float32, device=Ah.device) if out is None else _req(out, "out")
+    _check(lib().wp_facewise(_ptr(Ah), _ptr(Bh), _ptr(C), n1, n2, n4, p, int(transA), int(transB), pr,
+                             _ptr(ws), ws.numel(), _stream()), "wp_facewise")
+    return C
+
+
+def wp_wprod_workspace(n1, n2, n4, p, L, prec="fp32"):
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_wprod_workspace(n1, n2, n4, p, L, _prec(prec), ctypes.byref(nbytes)), "wp_wprod_workspace")
+    return nbytes.value
+
+
+def wp_wprod(A, B, L, transA=False, transB=False, prec="fp32", out=None, ws=None):
+    """C = op(A) *w op(B) (Def. 2.1) on the GPU."""
+    _req(A, "A"), _req(B, "B")
+    p, n1, n2, n4 = _prod_dims(A, B, transA, transB)
+    pr = _prec(prec)
+    need = wp_wprod_workspace(n1, n2, n4, p, L, pr)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, A.device)
+    C = torch.empty((p, n1, n4), dtype=torch.float32, device=A.device) if out is None else _req(out, "out")
+    _check(lib().wp_wprod(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, int(transA), int(transB), pr,
+                          _ptr(ws), ws.numel(), _stream()), "wp_wprod")
+    return C
+
+
+def wp_wprod_backward(A, B, G, L, need_dA=True, need_dB=True, prec="fp32", ws=None):
+    """(dA, dB) of <G, A *w B> by the adjoint route."""
+    _req(A, "A"), _req(B, "B"), _req(G, "G")
+    p, n1, n2 = A.shape
+    n4 = B.shape[2]
+    if B.shape[:2] != (p, n2) or tuple(G.shape) != (p, n1, n4):
+        raise ValueError("shape mismatch in wp_wprod_backward")
+    pr = _prec(prec)
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_wprod_backward_workspace(n1, n2, n4, p, L, pr, ctypes.byref(nbytes)),
+           "wp_wprod_backward_workspace")
+    if ws is None or ws.numel() < nbytes.value:
+        ws = _workspace(nbytes.value, A.device)
+    dA = torch.empty_like(A) if need_dA else None
+    dB = torch.empty_like(B) if need_dB else None
+    _check(lib().wp_wprod_backward(_ptr(A), _ptr(B), _ptr(G), _ptr(dA), _ptr(dB), n1, n2, n4, p, L, pr,
+                                   _ptr(ws), ws.numel(), _stream()), "wp_wprod_backward")
+    return dA, dB
+
+
+# ---- w-svd / sp-w-svd ------------------------------------------------------------
+
+def wp_wsvd(A, L, r, sparse=False, factors=False, factors_in_wavelet_domain=True, ws=None):
+    """Rank-r w-svd (sparse=False) or sp-w-svd (sparse=True) of A (p, n1, n2).
+
+    Returns C_r, or (C_r, U, S, V) with factors=True."""
+    _req(A, "A")
+    p, n1, n2 = A.shape
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_wsvd_workspace(n1, n2, p, L, r, ctypes.byref(nbytes)), "wp_wsvd_workspace")
+    if ws is None or ws.numel() < nbytes.value:
+        ws = _workspace(nbytes.value, A.device)
+    C = torch.empty_like(A)
+    U = S = V = None
+    if factors:
+        U = torch.empty((p, n1, r), dtype=torch.float32, device=A.device)
+        S = torch.empty((p, r), dtype=torch.float32, device=A.device)
+        V = torch.empty((p, n2, r), dtype=torch.float32, device=A.device)
+    _check(lib().wp_wsvd(_ptr(A), _ptr(C), _ptr(U), _ptr(S), _ptr(V), n1, n2, p, L, r, int(bool(sparse)),
+                         int(bool(factors_in_wavelet_domain)), _ptr(ws), ws.numel(), _stream()), "wp_wsvd")
+    return (C, U, S, V) if factors else C
+
+
+# ---- Moore-Penrose inverse ----------------------------------------------------------
+
+def wp_wpinv(A, L, rtol=-1.0, refine_iters=0, ws=None):
+    _req(A, "A")
+    p, m, n = A.shape
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_wpinv_workspace(m, n, p, L, ctypes.byref(nbytes)), "wp_wpinv_workspace")
+    if ws is None or ws.numel() < nbytes.value:
+        ws = _workspace(nbytes.value, A.device)
+    X = torch.empty((p, n, m), dtype=torch.float32, device=A.device)
+    _check(lib().wp_wpinv(_ptr(A), _ptr(X), m, n, p, L, float(rtol), int(refine_iters), _ptr(ws), ws.numel(),
+                          _stream()), "wp_wpinv")
+    return X
+
+
+def wp_profile_begin():
+    _check(lib().wp_profile_begin(), "wp_profile_begin")
+
+
+def wp_profile_end():
+    """Stop per-kernel timing; return {kernel name: (launches, total ms)}."""
+    _check(lib().wp_profile_end(), "wp_profile_end")
+    out = {}
+    buf = ctypes.create_string_buffer(128)
+    n, ms = _I64(0), ctypes.c_double(0.0)
+    for i in range(lib().wp_profile_count()):
+        _check(lib().wp_profile_get(i, buf, 128, ctypes.byref(n), ctypes.byref(ms)), "wp_profile_get")
+        out[buf.value.decode()] = (int(n.value), float(ms.value))
+    return out
+
+
+def wp_launch_count():
+    return int(lib().wp_launch_count())
+
+
+def wp_get_device_error():
+    return lib().wp_get_device_error(_stream())

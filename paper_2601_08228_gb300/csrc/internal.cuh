@@ -1,0 +1,25 @@
+// Internal (non-ABI) entry points shared between the library's translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace wp {
+
+enum LiftOpId { LIFT_FWD = 0, LIFT_INV = 1, LIFT_ADJ = 2, LIFT_IADJ = 3 };
+
+// Fused L-level lifting of a (p, plane) tensor; see lift.cu.
+int lift_dispatch(int op, const float* in, float* out, int64_t plane, int64_t p, int L,
+                  cudaStream_t st);
+
+// Plain FP32 SIMT batched GEMM; see gemm_simt.cu.
+int sgemm_batched(const float* A, const float* B, float* C, int M, int N, int K, bool transA,
+                  bool transB, int batch, cudaStream_t st);
+
+// Tensor-core face-products (BF16, BF16x3, FP8) of FP32 wavelet-domain
+// operands; see gemm_tc.cu.  Workspace holds the converted operands.
+size_t tc_facewise_workspace(int64_t M, int64_t N, int64_t K, int64_t p, int prec);
+int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K,
+                int64_t p, bool transA, bool transB, int prec, void* ws, size_t ws_bytes,
+                cudaStream_t st);
+
+}  // namespace wp

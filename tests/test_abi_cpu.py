@@ -1,0 +1,54 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/wprod.h declares, and rejects bad arguments on the
+host before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libwprod():
+    from paper_2601_08228_gb300 import build
+    build.build()
+    from paper_2601_08228_gb300 import capi
+    return capi.lib()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "wprod.h")).read()
+    return sorted(set(re.findall(r"WP_API\s+(?:const\s+char\s*\*|int|uint64_t)\s+(wp_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(libwprod):
+    names = _declared_symbols()
+    assert len(names) >= 23
+    for n in names:
+        assert hasattr(libwprod, n), n
+
+
+def test_status_strings_and_version(libwprod):
+    assert libwprod.wp_status_string(0) == b"WP_OK"
+    for code in range(1, 13):
+        assert libwprod.wp_status_string(code).startswith(b"WP_ERR_")
+    assert libwprod.wp_version() >= 100
+
+
+def test_host_validation_needs_no_gpu(libwprod):
+    L = libwprod
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: validation fails first
+    assert L.wp_lift_forward(None, fake, 4, 4, 8, 3, None) == 1          # NULL
+    assert L.wp_lift_forward(fake, ctypes.c_void_p(2 << 20), 4, 4, 12, 3, None) == 3  # p % 2^L
+    assert L.wp_lift_forward(fake, ctypes.c_void_p(2 << 20), 4, 4, 8, -1, None) == 3
+    assert L.wp_lift_forward(fake, ctypes.c_void_p(2 << 20), 0, 4, 8, 3, None) == 2   # shape
+    assert L.wp_lift_forward(fake, ctypes.c_void_p((2 << 20) + 4), 4, 4, 8, 3, None) == 6  # align
+    assert L.wp_lift_forward(fake, fake, 4, 4, 8, 3, None) == 11         # alias
+    n = ctypes.c_size_t(0)
+    assert L.wp_wprod_workspace(4, 4, 4, 8, 3, 9, ctypes.byref(n)) == 5  # prec
+    assert L.wp_wprod_workspace(4, 4, 4, 8, 3, 0, ctypes.byref(n)) == 0 and n.value > 0
+    assert L.wp_wprod(fake, ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), 4, 4, 4, 8, 3, 0, 0, 0,
+                      ctypes.c_void_p(4 << 20), 16, None) == 7           # workspace too small
