@@ -1,0 +1,117 @@
+"""GPU parity of the tcgen05 tensor-core face-products (BF16, BF16x3) and of
+the mixed-precision w-product, against the FP64 oracle.  BF16x3 is gated at
+the product bar (1e-5 relative Frobenius); single BF16 is reported, and only
+checked loosely (1e-2) to show it computes the right product."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2601_08228_gb300 import capi, synth
+from tests import _golden
+
+pytestmark = pytest.mark.gpu
+
+TOL_X3 = 1e-5
+TOL_BF16 = 1e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2601_08228_gb300 import build
+    build.build()
+    capi.lib()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rand(shape, seed):
+    return np.random.default_rng(seed).standard_normal(size=shape).astype(np.float32)
+
+
+FACE_CASES = [
+    # p, M, N, K
+    (4, 128, 128, 64),      # exactly one tile
+    (3, 200, 300, 100),     # ragged M, N, K
+    (2, 1, 1, 1),           # degenerate
+    (2, 5, 7, 7),           # K not a multiple of 8 (padded row stride)
+    (5, 256, 256, 256),
+    (1, 1000, 520, 1030),   # many tiles, ragged everywhere
+    (8, 64, 32, 512),       # long K, narrow tile
+]
+
+
+@pytest.mark.parametrize("p,M,N,K", FACE_CASES)
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_facewise_tc(p, M, N, K, prec):
+    A, B = rand((p, M, K), 1), rand((p, K, N), 2)
+    C = host(capi.wp_facewise(dev(A), dev(B), prec=prec))
+    err = O.rel_fro(C, O.facewise(A, B))
+    assert err <= (TOL_X3 if prec == "bf16x3" else TOL_BF16), err
+
+
+@pytest.mark.parametrize("tA,tB", [(True, False), (False, True), (True, True)])
+def test_facewise_tc_transposes(tA, tB):
+    p, M, N, K = 3, 130, 70, 90
+    A = rand((p, K, M) if tA else (p, M, K), 3)
+    B = rand((p, N, K) if tB else (p, K, N), 4)
+    C = host(capi.wp_facewise(dev(A), dev(B), transA=tA, transB=tB, prec="bf16x3"))
+    At = np.swapaxes(A, 1, 2) if tA else A
+    Bt = np.swapaxes(B, 1, 2) if tB else B
+    assert O.rel_fro(C, O.facewise(At, Bt)) <= TOL_X3
+
+
+def test_wprod_example_2_2_bit_exact_tc():
+    """Small dyadic inputs are exact in BF16 (lo = 0), so the worked example
+    is reproduced bit for bit by both tensor-core modes."""
+    ex = _golden.load("example_2_2.txt")
+    for prec in ("bf16", "bf16x3"):
+        C = host(capi.wp_wprod(dev(ex["A"]), dev(ex["B"]), 2, prec=prec))
+        np.testing.assert_array_equal(C, ex["C"])
+
+
+def test_wprod_bf16x3_plain_32x32x16():
+    A, B = synth.plain_pair(32, 32, 32, 16, seed=0)
+    C = host(capi.wp_wprod(dev(A), dev(B), 2, prec="bf16x3"))
+    assert O.rel_fro(C, O.wprod(A, B, 2)) <= TOL_X3
+
+
+@pytest.mark.parametrize("p,n1,n2,n4,L", [(24, 33, 17, 45, 3), (64, 130, 129, 131, 4), (96, 16, 24, 8, 5)])
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, True)])
+def test_wprod_bf16x3_parity(p, n1, n2, n4, L, tA, tB):
+    A = rand((p, n2, n1) if tA else (p, n1, n2), 5)
+    B = rand((p, n4, n2) if tB else (p, n2, n4), 6)
+    C = host(capi.wp_wprod(dev(A), dev(B), L, transA=tA, transB=tB, prec="bf16x3"))
+    assert O.rel_fro(C, O.wprod(A, B, L, transA=tA, transB=tB)) <= TOL_X3
+
+
+def test_wprod_bf16x3_full_size_sampled():
+    """256x256x192, L = 3, the benchmark's launch configuration; sampled
+    16 rows x 16 columns of C against the oracle."""
+    n, p, L = 256, 192, 3
+    A = synth.hsi_cube(n, n, p, seed=0, dtype=np.float32)
+    B = synth.hsi_cube(n, n, p, seed=1, dtype=np.float32)
+    C = host(capi.wp_wprod(dev(A), dev(B), L, prec="bf16x3"))
+    rng = np.random.default_rng(12)
+    rows = np.sort(rng.choice(n, 16, replace=False))
+    cols = np.sort(rng.choice(n, 16, replace=False))
+    ref = O.wprod(A[:, rows, :], B[:, :, cols], L)
+    assert O.rel_fro(C[:, rows][:, :, cols], ref) <= TOL_X3
+
+
+def test_backward_bf16x3_parity():
+    p, n1, n2, n4, L = 32, 48, 80, 40, 4
+    A, B, G = rand((p, n1, n2), 7), rand((p, n2, n4), 8), rand((p, n1, n4), 9)
+    dA, dB = capi.wp_wprod_backward(dev(A), dev(B), dev(G), L, prec="bf16x3")
+    rA, rB = O.wprod_grad(A, B, G, L)
+    assert O.rel_fro(host(dA), rA) <= TOL_X3
+    assert O.rel_fro(host(dB), rB) <= TOL_X3
+    assert capi.wp_get_device_error() == 0
