@@ -148,6 +148,33 @@ WP_API int wp_wprod(const float* A, const float* B, float* C, int64_t n1, int64_
              int64_t p, int L, int transA, int transB, int prec, void* ws, size_t ws_bytes,
              void* stream);
 
+/* ---- w-product without a caller-supplied workspace ---------------------- */
+
+/* Size in bytes of the library-owned scratch array used by wp_wprod_noalloc. */
+#define WP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Same result as wp_wprod, for callers that cannot allocate device memory
+ * for a workspace: plain C hosts without a device allocator, or plug-ins
+ * whose host application owns every device allocation.  The paper has no
+ * counterpart to this call; it only changes where the scratch space lives.
+ *
+ * The scratch space is one fixed array of WP_NOALLOC_SCRATCH_BYTES bytes in
+ * device global memory, created when the library is loaded and held by every
+ * GPU that loads it until the process exits.  The call allocates nothing;
+ * the caller still owns and passes A, B and C.
+ *   - Requests whose wp_wprod_workspace() size exceeds the array return
+ *     WP_ERR_WORKSPACE and launch nothing.
+ *   - The first call on each device looks up the array's device address on
+ *     that device (the device current at the time of the call).
+ *   - All calls share the one array.  Calls whose kernels overlap on the GPU
+ *     (different streams, or different host threads on one device) race on
+ *     it and give wrong results: serialise them, e.g. on one stream.
+ *   - The array keeps whatever the last call left in it; every byte a call
+ *     reads is written earlier in that same call, so no clearing is needed. */
+WP_API int wp_wprod_noalloc(const float* A, const float* B, float* C, int64_t n1, int64_t n2,
+                            int64_t n4, int64_t p, int L, int transA, int transB, int prec,
+                            void* stream);
+
 /* ---- a6: backward of C = A *w B (adjoint route) ------------------------- */
 
 /* Given G = dLoss/dC (p, n1, n4), computes

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "wp_facewise": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _P, _SZ, _P], _I),
     "wp_wprod_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wprod": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _I, _P, _SZ, _P], _I),
+    "wp_wprod_noalloc": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _I, _P], _I),
     "wp_wprod_backward_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wprod_backward": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "wp_wsvd_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
@@ -184,6 +185,17 @@ def wp_wprod(A, B, L, transA=False, transB=False, prec="fp32", out=None, ws=None
     C = torch.empty((p, n1, n4), dtype=torch.float32, device=A.device) if out is None else _req(out, "out")
     _check(lib().wp_wprod(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, int(transA), int(transB), pr,
                           _ptr(ws), ws.numel(), _stream()), "wp_wprod")
+    return C
+
+
+def wp_wprod_noalloc(A, B, L, transA=False, transB=False, prec="fp32", out=None):
+    """C = op(A) *w op(B) using the library's own fixed scratch array instead
+    of a workspace (for callers that cannot allocate device memory)."""
+    _req(A, "A"), _req(B, "B")
+    p, n1, n2, n4 = _prod_dims(A, B, transA, transB)
+    C = torch.empty((p, n1, n4), dtype=torch.float32, device=A.device) if out is None else _req(out, "out")
+    _check(lib().wp_wprod_noalloc(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, int(transA), int(transB),
+                                  _prec(prec), _stream()), "wp_wprod_noalloc")
     return C
 
 
