@@ -23,3 +23,15 @@ int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, 
                 cudaStream_t st);
 
 }  // namespace wp
+
+namespace wp {
+
+// Batched one-sided Jacobi SVD (jacobi.cu): leading r singular triplets of
+// slices [slice0, slice0 + nslices) of X (p, n1, n2).  vec_out (p, max(n1,n2), r)
+// receives unit left vectors when n1 >= n2, unit right vectors otherwise;
+// sig_out (p, r) the singular values in descending order.
+int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, float* vec_out, float* sig_out,
+               cudaStream_t st);
+bool jacobi_supported(int n1, int n2);
+
+}  // namespace wp
