@@ -14,15 +14,18 @@
 // Parallel ordering: round-robin "circle" tournament, n_pad - 1 rounds of
 // n_pad / 2 disjoint pairs per sweep.  A slice is held in shared memory,
 // split by rows across a thread-block cluster of CL CTAs (CL = 1, 2, 4, 8);
-// each warp owns pairs, computes its rows' partial dot product with lane
-// strides and a shuffle reduction, and publishes the partial to every CTA of
+// each warp computes its pairs' partial dot products over the CTA's rows, and publishes the partial to every CTA of
 // the cluster through distributed shared memory (double-buffered per round,
 // one cluster barrier per round).  Every CTA then sums the partials in rank
 // order -- bit-identical totals, hence identical rotation decisions across
-// the cluster -- and rotates its own rows.  Column norms are tracked with
+// the cluster -- and rotates its own rows.  Within a CTA a warp owns up to 8
+// pairs of a round: its lanes sweep consecutive rows (no shared-memory bank
+// conflicts), the pairs are independent instruction streams, and one
+// multi-value butterfly reduces all of them.  Column norms are tracked with
 // alpha' = alpha - t gamma, beta' = beta + t gamma and recomputed exactly at
 // the start of every sweep.  A sweep with no rotation above the threshold
-// |gamma| > tol sqrt(alpha beta) ends the iteration; reaching max_sweeps sets
+// |gamma| > tol sqrt(alpha beta) (tol = 2 sqrt(m_len) eps) ends the
+// iteration; reaching max_sweeps sets
 // WP_ERR_NOT_CONVERGED in the device status word (results are still written).
 //
 // The rotation angle is computed in FP32 with the stable formula above: on
@@ -38,8 +41,7 @@ namespace cg = cooperative_groups;
 
 namespace wp {
 
-constexpr int JAC_THREADS = 256;
-constexpr int JAC_WARPS = JAC_THREADS / 32;
+constexpr int JAC_THREADS = 512;
 
 struct JacobiArgs {
   const float* X;      // slices (p, n1, n2)
@@ -57,7 +59,11 @@ struct JacobiArgs {
 
 __device__ __forceinline__ void pair_of(int i, int k, int n, int& a, int& b) {
   // circle method: position 0 fixed, positions 1..n-1 rotate by k
-  auto elem = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + k) % (n - 1); };
+  auto elem = [&](int pos) {
+    int q = pos - 1 + k;
+    q -= (q >= n - 1) ? (n - 1) : 0;
+    return pos == 0 ? 0 : 1 + q;
+  };
   a = elem(i);
   b = elem(n - 1 - i);
 }
@@ -68,20 +74,6 @@ __device__ __forceinline__ void cluster_barrier() {
   else __syncthreads();
 }
 
-// Publish `val` as this CTA's partial for entry i of buffer `buf`.
-template <int CL>
-__device__ __forceinline__ void publish(float* part, int buf, int rank, int n_pad, int i, float val, int lane) {
-  float* local = part + (size_t(buf) * CL + rank) * n_pad + i;
-  if constexpr (CL == 1) {
-    if (lane == 0) *local = val;
-  } else {
-    if (lane < CL) {
-      float* remote = cg::this_cluster().map_shared_rank(local, lane);
-      *remote = val;
-    }
-  }
-}
-
 template <int CL>
 __device__ __forceinline__ float gather(const float* part, int buf, int n_pad, int i) {
   float s = 0.f;
@@ -90,15 +82,48 @@ __device__ __forceinline__ float gather(const float* part, int buf, int n_pad, i
   return s;
 }
 
-template <int CL>
+// Sum PPW per-lane values over the 32 lanes of a warp with a multi-value
+// butterfly: after the call, lane l holds the warp total of value
+// (l >> (5 - log2 PPW)).  log2(PPW) + (5 - log2 PPW) shuffle stages, 2 PPW - 1
+// + (5 - log2 PPW) shuffles in all (9 for PPW = 8, instead of 40).
+template <int PPW>
+__device__ __forceinline__ float multi_reduce(float (&v)[PPW], int lane) {
+  int c = PPW;
+  int d = 16;
+#pragma unroll
+  for (int step = 0; (1 << step) < PPW; ++step) {
+    c >>= 1;
+    const bool upper = (lane & d) != 0;
+#pragma unroll
+    for (int i = 0; i < PPW / 2; ++i) {
+      if (i < c) {
+        const float send = upper ? v[i] : v[i + c];
+        const float keep = upper ? v[i + c] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+      }
+    }
+    d >>= 1;
+  }
+  float t = v[0];
+#pragma unroll
+  for (; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+  return t;
+}
+
+// One warp owns PPW column pairs of a round; its 32 lanes sweep consecutive
+// rows (conflict-free shared-memory access) and the PPW pairs form
+// independent instruction streams.  RPL rows per lane per chunk.
+template <int CL, int PPW, int RPL>
 __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   extern __shared__ float sm[];
-  const int n_pad = a.n_pad, rpc = a.rpc;
+  const int n_pad = a.n_pad, rpc = a.rpc, npairs = n_pad / 2;
   float* Xs = sm;                                     // [n_pad][rpc], column-major
   float* norms = Xs + size_t(n_pad) * rpc;            // [n_pad]
   float* part = norms + n_pad;                        // [2][CL][n_pad]
   int* order = reinterpret_cast<int*>(part + 2 * CL * n_pad);   // [n_pad]
-  __shared__ int rot_count;
+  constexpr int NW = JAC_THREADS / 32;
+  constexpr int LPP = 32 / PPW;                       // lanes holding one pair's total
+  constexpr int SHIFT = (PPW == 1) ? 5 : (PPW == 2) ? 4 : (PPW == 4) ? 3 : (PPW == 8) ? 2 : 1;
 
   const int rank = (CL > 1) ? int(cg::this_cluster().block_rank()) : 0;
   const int slice = a.slice0 + int(blockIdx.x) / CL;
@@ -106,7 +131,6 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   const float* A = a.X + int64_t(slice) * a.n1 * a.n2;
   const int row0 = rank * rpc;
 
-  // load this CTA's rows of the working matrix (zero padding rows / column)
   for (int idx = threadIdx.x; idx < n_pad * rpc; idx += JAC_THREADS) {
     const int c = idx / rpc, rr = idx % rpc, R = row0 + rr;
     float v = 0.f;
@@ -115,14 +139,34 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   }
   __syncthreads();
 
+  // publish the warp's PPW totals: lane l holds entry `base + (l >> SHIFT) * stride`
+  auto publish_warp = [&](int buf, float total, int first, int stride, int limit) {
+    const int j = lane >> SHIFT;
+    const int e = first + j * stride;
+    if (e < limit) {
+      for (int q = lane & (LPP - 1); q < CL; q += LPP) {
+        float* local = part + (size_t(buf) * CL + rank) * n_pad + e;
+        if constexpr (CL == 1) *local = total;
+        else *cg::this_cluster().map_shared_rank(local, q) = total;
+      }
+    }
+  };
+
   auto exact_norms = [&](int buf) {
-    for (int c = warp; c < n_pad; c += JAC_WARPS) {
-      const float* col = Xs + size_t(c) * rpc;
-      float s = 0.f;
-      for (int rr = lane; rr < rpc; rr += 32) s = fmaf(col[rr], col[rr], s);
+    // warp w handles columns w + NW * (j + PPW * it)
+    for (int base = 0; base < n_pad; base += NW * PPW) {
+      float acc[PPW];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      publish<CL>(part, buf, rank, n_pad, c, s, lane);
+      for (int j = 0; j < PPW; ++j) {
+        acc[j] = 0.f;
+        const int c = base + warp + j * NW;
+        if (c < n_pad) {
+          const float* col = Xs + size_t(c) * rpc;
+          for (int rr = lane; rr < rpc; rr += 32) acc[j] = fmaf(col[rr], col[rr], acc[j]);
+        }
+      }
+      const float t = multi_reduce<PPW>(acc, lane);
+      publish_warp(buf, t, base + warp, NW, n_pad);
     }
     cluster_barrier<CL>();
     for (int c = threadIdx.x; c < n_pad; c += JAC_THREADS) norms[c] = gather<CL>(part, buf, n_pad, c);
@@ -134,57 +178,108 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     exact_norms(buf);
     buf ^= 1;
-    if (threadIdx.x == 0) rot_count = 0;
-    __syncthreads();
+    int rotated_sweep = 0;
     for (int k = 0; k < n_pad - 1; ++k) {
-      // partial dot products of this CTA's rows
-      for (int i = warp; i < n_pad / 2; i += JAC_WARPS) {
-        int ca, cb;
-        pair_of(i, k, n_pad, ca, cb);
-        const float* xa = Xs + size_t(ca) * rpc;
-        const float* xb = Xs + size_t(cb) * rpc;
-        float g = 0.f;
-        for (int rr = lane; rr < rpc; rr += 32) g = fmaf(xa[rr], xb[rr], g);
+      int rotated = 0;
+      for (int base = 0; base < npairs; base += NW * PPW) {
+        // ---- partial dot products of this CTA's rows, PPW independent chains
+        int ca[PPW], cb[PPW];
+        float acc[PPW];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-        publish<CL>(part, buf, rank, n_pad, i, g, lane);
-      }
-      cluster_barrier<CL>();
-      // identical rotation decisions on every CTA; each rotates its own rows
-      int local_rot = 0;
-      for (int i = warp; i < n_pad / 2; i += JAC_WARPS) {
-        int ca, cb;
-        pair_of(i, k, n_pad, ca, cb);
-        const float g = gather<CL>(part, buf, n_pad, i);
-        const float al = norms[ca], be = norms[cb];
-        if (g != 0.f && fabsf(g) > a.tol * sqrtf(al) * sqrtf(be)) {
-          const float zeta = (be - al) / (2.f * g);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-          const float c = rsqrtf(fmaf(t, t, 1.f));
-          const float s = c * t;
-          float* xa = Xs + size_t(ca) * rpc;
-          float* xb = Xs + size_t(cb) * rpc;
-          for (int rr = lane; rr < rpc; rr += 32) {
-            const float u = xa[rr], v = xb[rr];
-            xa[rr] = fmaf(c, u, -s * v);
-            xb[rr] = fmaf(s, u, c * v);
-          }
-          __syncwarp();
-          if (lane == 0) {
-            norms[ca] = fmaf(-t, g, al);
-            norms[cb] = fmaf(t, g, be);
-          }
-          ++local_rot;
+        for (int j = 0; j < PPW; ++j) {
+          const int i = base + warp + j * NW;
+          acc[j] = 0.f;
+          ca[j] = cb[j] = 0;
+          if (i < npairs) pair_of(i, k, n_pad, ca[j], cb[j]);
         }
+        // RPL > 0: the pair's rows stay in registers from the dot product to
+        // the rotation (4 shared-memory accesses per element pair, not 6)
+        float ru[PPW][RPL > 0 ? RPL : 1], rv[PPW][RPL > 0 ? RPL : 1];
+        if constexpr (RPL > 0) {
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            const int rr = lane + 32 * q;
+#pragma unroll
+            for (int j = 0; j < PPW; ++j) {
+              const bool in = rr < rpc;
+              ru[j][q] = in ? Xs[size_t(ca[j]) * rpc + rr] : 0.f;
+              rv[j][q] = in ? Xs[size_t(cb[j]) * rpc + rr] : 0.f;
+              acc[j] = fmaf(ru[j][q], rv[j][q], acc[j]);
+            }
+          }
+        } else {
+          for (int rr = lane; rr < rpc; rr += 32) {
+#pragma unroll
+            for (int j = 0; j < PPW; ++j)
+              acc[j] = fmaf(Xs[size_t(ca[j]) * rpc + rr], Xs[size_t(cb[j]) * rpc + rr], acc[j]);
+          }
+        }
+        const float tot = multi_reduce<PPW>(acc, lane);
+        publish_warp(buf, tot, base + warp, NW, npairs);
+        cluster_barrier<CL>();
+        // ---- rotation: lane quad of pair j computes its angle, then broadcast
+        const int jm = lane >> SHIFT;
+        const int im = base + warp + jm * NW;
+        float cm = 1.f, sm_ = 0.f;
+        if (im < npairs) {
+          int xa, xb;
+          pair_of(im, k, n_pad, xa, xb);
+          const float g = gather<CL>(part, buf, n_pad, im);
+          const float al = norms[xa], be = norms[xb];
+          if (g != 0.f && fabsf(g) > a.tol * sqrtf(al * be)) {
+            // stable angle; c^2 + s^2 = 1 holds whatever the rounding of t
+            const float zeta = __fdividef(be - al, 2.f * g);
+            const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            cm = rsqrtf(fmaf(t, t, 1.f));
+            sm_ = cm * t;
+            rotated = 1;
+            if ((lane & (LPP - 1)) == 0) {
+              norms[xa] = fmaf(-t, g, al);
+              norms[xb] = fmaf(t, g, be);
+            }
+          }
+        }
+        float cj[PPW], sj[PPW];
+#pragma unroll
+        for (int j = 0; j < PPW; ++j) {
+          cj[j] = __shfl_sync(0xffffffffu, cm, j << SHIFT);
+          sj[j] = __shfl_sync(0xffffffffu, sm_, j << SHIFT);
+        }
+        if constexpr (RPL > 0) {
+#pragma unroll
+          for (int j = 0; j < PPW; ++j) {
+            if (sj[j] != 0.f) {
+#pragma unroll
+              for (int q = 0; q < RPL; ++q) {
+                const int rr = lane + 32 * q;
+                if (rr < rpc) {
+                  const float u = ru[j][q], v = rv[j][q];
+                  Xs[size_t(ca[j]) * rpc + rr] = fmaf(cj[j], u, -sj[j] * v);
+                  Xs[size_t(cb[j]) * rpc + rr] = fmaf(sj[j], u, cj[j] * v);
+                }
+              }
+            }
+          }
+        } else {
+          for (int rr = lane; rr < rpc; rr += 32) {
+#pragma unroll
+            for (int j = 0; j < PPW; ++j) {
+              if (sj[j] != 0.f) {
+                float* xa = Xs + size_t(ca[j]) * rpc + rr;
+                float* xb = Xs + size_t(cb[j]) * rpc + rr;
+                const float u = *xa, v = *xb;
+                *xa = fmaf(cj[j], u, -sj[j] * v);
+                *xb = fmaf(sj[j], u, cj[j] * v);
+              }
+            }
+          }
+        }
+        buf ^= 1;
+        if (base + NW * PPW < npairs) __syncthreads();
       }
-      if (lane == 0 && local_rot) atomicAdd(&rot_count, local_rot);
-      buf ^= 1;
-      __syncthreads();
+      rotated_sweep |= __syncthreads_or(rotated);
     }
-    __syncthreads();
-    const int rc = rot_count;
-    __syncthreads();
-    if (rc == 0) { converged = true; break; }
+    if (!rotated_sweep) { converged = true; break; }
   }
   if (!converged && threadIdx.x == 0 && rank == 0) report_device_error(a.status, WP_ERR_NOT_CONVERGED);
 
@@ -222,25 +317,24 @@ static size_t jacobi_smem(int n_pad, int rpc, int CL) {
 
 constexpr size_t JAC_SMEM_MAX = 200 * 1024;
 
-// Pick the cluster size: the smallest that fits shared memory, grown (while
-// every CTA keeps at least 32 rows) until the launch has >= 4 CTAs per SM.
-static int pick_cluster(int m_len, int n_pad, int nslices) {
-  int chosen = -1;
+// Pick the cluster size: the smallest that fits the slice in shared memory.
+// A round is latency-bound (two barriers and a short dependency chain), so
+// splitting a slice over more CTAs barely shortens it while multiplying the
+// CTAs that must be resident; measured on 256 x 256 slices, 2-CTA clusters
+// finish 192 slices twice as fast as 4-CTA clusters.
+static int pick_cluster(int m_len, int n_pad, int /*nslices*/) {
   for (int CL = 1; CL <= 8; CL *= 2) {
     const int rpc = (m_len + CL - 1) / CL;
-    if (jacobi_smem(n_pad, rpc, CL) > JAC_SMEM_MAX) continue;
-    if (chosen > 0 && rpc < 32) break;
-    chosen = CL;
-    if (int64_t(nslices) * CL >= 4 * int64_t(sm_count())) break;
+    if (jacobi_smem(n_pad, rpc, CL) <= JAC_SMEM_MAX) return CL;
   }
-  return chosen;
+  return -1;
 }
 
-template <int CL>
+template <int CL, int PPW, int RPL>
 static int launch_jacobi(const JacobiArgs& args, int nslices, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    WP_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WP_CUDA_TRY(cudaFuncSetAttribute(jacobi_kernel<CL, PPW, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(JAC_SMEM_MAX + 4096)));
     attr = true;
   }
@@ -257,8 +351,29 @@ static int launch_jacobi(const JacobiArgs& args, int nslices, size_t smem, cudaS
   cfg.attrs = attrs;
   cfg.numAttrs = 1;
   WP_PROFILE("jacobi_svd", st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_kernel<CL>, args));
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_kernel<CL, PPW, RPL>, args));
   return launch_status();
+}
+
+template <int CL, int PPW>
+static int launch_jacobi_rpl(const JacobiArgs& args, int nslices, size_t smem, cudaStream_t st) {
+  // rows per lane kept in registers (RPL * PPW * 2 values); 0 = reload path
+  const int rpl = (args.rpc + 31) / 32;
+  if (rpl <= 1) return launch_jacobi<CL, PPW, 1>(args, nslices, smem, st);
+  if (rpl <= 2) return launch_jacobi<CL, PPW, 2>(args, nslices, smem, st);
+  if (rpl <= 4 && PPW <= 8) return launch_jacobi<CL, PPW, 4>(args, nslices, smem, st);
+  return launch_jacobi<CL, PPW, 0>(args, nslices, smem, st);
+}
+
+template <int CL>
+static int launch_jacobi_lg(const JacobiArgs& args, int nslices, size_t smem, cudaStream_t st) {
+  // pairs per warp: enough that one pass covers a round (at most 8)
+  const int npairs = args.n_pad / 2;
+  const int nw = JAC_THREADS / 32;
+  if (npairs <= nw) return launch_jacobi_rpl<CL, 1>(args, nslices, smem, st);
+  if (npairs <= 2 * nw) return launch_jacobi_rpl<CL, 2>(args, nslices, smem, st);
+  if (npairs <= 4 * nw) return launch_jacobi_rpl<CL, 4>(args, nslices, smem, st);
+  return launch_jacobi_rpl<CL, 8>(args, nslices, smem, st);
 }
 
 // Leading r singular triplets of slices [slice0, slice0 + nslices) of X
@@ -288,10 +403,10 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
   a.rpc = (a.m_len + CL - 1) / CL;
   const size_t smem = jacobi_smem(a.n_pad, a.rpc, CL);
   switch (CL) {
-    case 1: return launch_jacobi<1>(a, nslices, smem, st);
-    case 2: return launch_jacobi<2>(a, nslices, smem, st);
-    case 4: return launch_jacobi<4>(a, nslices, smem, st);
-    default: return launch_jacobi<8>(a, nslices, smem, st);
+    case 1: return launch_jacobi_lg<1>(a, nslices, smem, st);
+    case 2: return launch_jacobi_lg<2>(a, nslices, smem, st);
+    case 4: return launch_jacobi_lg<4>(a, nslices, smem, st);
+    default: return launch_jacobi_lg<8>(a, nslices, smem, st);
   }
 }
 
