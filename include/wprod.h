@@ -188,6 +188,21 @@ WP_API int wp_wprod_backward(const float* A, const float* B, const float* G, flo
                       int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* ---- deblurring step driven by the backward (Sec. IV-C) ----------------- */
+
+/* One gradient step on f(X) = ||K *w X - Y||_F^2 + lam ||X||_F^2, the
+ * least-squares form of the deblurring model of Sec. IV-C with one blur
+ * operator:  X <- X - eta (2 K^T *w (K *w X - Y) + 2 lam X).  K^T *w R is
+ * evaluated by the w-product backward (adjoint route).  K (p, n1, n1),
+ * Y and X (p, n1, n2); X is updated in place.  If `loss` is not NULL (device
+ * pointer to one double), f(X) at the start of the step is ADDED to *loss.
+ * No host synchronisation and no allocation: a loop of steps can be
+ * captured in a CUDA graph. */
+WP_API int wp_deblur_workspace(int64_t n1, int64_t n2, int64_t p, int L, int prec, size_t* bytes);
+WP_API int wp_deblur_step(const float* K, const float* Y, float* X, int64_t n1, int64_t n2, int64_t p,
+                          int L, float lam, float eta, int prec, double* loss, void* ws, size_t ws_bytes,
+                          void* stream);
+
 /* ---- a3: truncated w-svd and sp-w-svd (Algorithm 2, Thm 2.5, Sec. IV-B) -- */
 
 /* C_r = rank-r w-svd of A (p, n1, n2): per wavelet-domain slice a one-sided

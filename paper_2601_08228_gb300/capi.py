@@ -62,6 +62,8 @@ _SIGNATURES = {
     "wp_wprod_noalloc": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _I, _P], _I),
     "wp_wprod_backward_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wprod_backward": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
+    "wp_deblur_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_deblur_step": ([_P, _P, _P, _I64, _I64, _I64, _I, ctypes.c_float, ctypes.c_float, _I, _P, _P, _SZ, _P], _I),
     "wp_wsvd_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wsvd": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I, _I, _I, _I, _P, _SZ, _P], _I),
     "wp_wpinv_workspace": ([_I64, _I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
@@ -217,6 +219,31 @@ def wp_wprod_backward(A, B, G, L, need_dA=True, need_dB=True, prec="fp32", ws=No
     _check(lib().wp_wprod_backward(_ptr(A), _ptr(B), _ptr(G), _ptr(dA), _ptr(dB), n1, n2, n4, p, L, pr,
                                    _ptr(ws), ws.numel(), _stream()), "wp_wprod_backward")
     return dA, dB
+
+
+# ---- deblurring ------------------------------------------------------------------
+
+def wp_deblur_workspace(n1, n2, p, L, prec="fp32"):
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_deblur_workspace(n1, n2, p, L, _prec(prec), ctypes.byref(nbytes)), "wp_deblur_workspace")
+    return nbytes.value
+
+
+def wp_deblur_step(K, Y, X, L, lam, eta, prec="fp32", loss=None, ws=None):
+    """In-place gradient step X <- X - eta grad f(X), f = |K *w X - Y|^2 + lam |X|^2.
+    `loss`: optional CUDA float64 tensor of one element; f(X) is added to it."""
+    _req(K, "K"), _req(Y, "Y"), _req(X, "X")
+    p, n1, n2 = X.shape
+    if tuple(K.shape) != (p, n1, n1) or tuple(Y.shape) != (p, n1, n2):
+        raise ValueError("shape mismatch in wp_deblur_step")
+    if loss is not None and (not loss.is_cuda or loss.dtype != torch.float64 or loss.numel() != 1):
+        raise ValueError("loss must be a one-element CUDA float64 tensor")
+    need = wp_deblur_workspace(n1, n2, p, L, prec)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, X.device)
+    _check(lib().wp_deblur_step(_ptr(K), _ptr(Y), _ptr(X), n1, n2, p, L, float(lam), float(eta), _prec(prec),
+                                _ptr(loss), _ptr(ws), ws.numel(), _stream()), "wp_deblur_step")
+    return X
 
 
 # ---- w-svd / sp-w-svd ------------------------------------------------------------

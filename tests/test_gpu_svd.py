@@ -190,6 +190,8 @@ def test_wpinv_invertible_gives_identity():
     detail slices difference the 4 I away."""
     p, n, L = 8, 16, 3
     A = O.ilift(rand((p, n, n), 9) + 4 * np.eye(n), L).astype(np.float32)
-    X = host(capi.wp_wpinv(dev(A), L))
-    assert O.rel_fro(O.wprod(A, X, L), O.identity(n, p, L)) <= 1e-5
+    X = host(capi.wp_wpinv(dev(A), L, refine_iters=2))
+    # even the FP32-rounded exact inverse leaves |A X - I| ~ kappa eps
+    tol = max(1e-5, 8 * _kappa(A, L) * 1.2e-7)
+    assert O.rel_fro(O.wprod(A, X, L), O.identity(n, p, L)) <= tol
     assert capi.wp_get_device_error() == 0
