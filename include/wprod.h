@@ -231,8 +231,9 @@ WP_API int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t p, i
 
 /* ---- a7: batched launch over many uneven tensors ------------------------ */
 
-/* One item: C = A *w B and C_r = rank-r w-svd of A, for A (p, n1, n2),
- * B (p, n2, n4), C (p, n1, n4), C_r (p, n1, n2); all device pointers. */
+/* One item: C = A *w B (Def. 2.1) and C_r = rank-r w-svd of A
+ * (Algorithm 2), for A (p, n1, n2), B (p, n2, n4), C (p, n1, n4),
+ * C_r (p, n1, n2); all device pointers, slice-major as everywhere. */
 typedef struct {
   const float* A;
   const float* B;
@@ -241,13 +242,31 @@ typedef struct {
   int32_t n1, n2, n4, p, L, r;
 } wp_batch_item;
 
-/* `items` is a HOST array of `count` descriptors; the call copies it into
- * the workspace (one cudaMemcpyAsync) and runs every item's w-product and
- * rank-r w-svd in persistent launches whose work lists are built on the
- * host.  Limits: 1 <= n1, n2, n4 <= 64 and r <= min(n1, n2). */
+/* Plan of a batched launch, filled by wp_batched_plan and passed unchanged
+ * to wp_batched_run.  Offsets are bytes into the workspace. */
+typedef struct {
+  int32_t count;
+  int32_t n_lift_fwd, n_lift_inv;
+  int32_t gemm_threads, svd_threads;   /* CTA sizes (autotuned when tune = 1) */
+  int64_t n_units;                     /* wavelet-domain slices over all items */
+  int64_t lift_fwd_blocks, lift_inv_blocks;
+  uint64_t items_off, lift_fwd_off, lift_inv_off, units_off;
+} wp_batch_plan;
+
+/* `items` is a HOST array of `count` descriptors (device pointers inside).
+ * Limits: 1 <= n1, n2, n4 <= 64, 0 <= L <= 5, p % 2^L == 0,
+ * 1 <= r <= min(n1, n2).  wp_batched_plan writes the work lists into the
+ * workspace (host-to-device copies, then a synchronisation of `stream`) and,
+ * with tune = 1, times candidate CTA sizes for the face-product and Jacobi
+ * phases on the planned work (this runs those phases; outputs are not
+ * final until wp_batched_run).  wp_batched_run launches the four phases
+ * (lifting, face-products, Jacobi SVD with rank-r rebuild, inverse lifting);
+ * it neither allocates, copies nor synchronises, so it can be captured in a
+ * CUDA graph and replayed while the workspace and the items' buffers live. */
 WP_API int wp_batched_workspace(const wp_batch_item* items, int count, size_t* bytes);
-WP_API int wp_batched(const wp_batch_item* items, int count, void* ws, size_t ws_bytes,
-               void* stream);
+WP_API int wp_batched_plan(const wp_batch_item* items, int count, int tune, void* ws, size_t ws_bytes,
+                           wp_batch_plan* plan, void* stream);
+WP_API int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,14 @@ class WPBatchItem(ctypes.Structure):
                 ("r", ctypes.c_int32)]
 
 
+class WPBatchPlan(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("n_lift_fwd", ctypes.c_int32), ("n_lift_inv", ctypes.c_int32),
+                ("gemm_threads", ctypes.c_int32), ("svd_threads", ctypes.c_int32), ("n_units", ctypes.c_int64),
+                ("lift_fwd_blocks", ctypes.c_int64), ("lift_inv_blocks", ctypes.c_int64),
+                ("items_off", ctypes.c_uint64), ("lift_fwd_off", ctypes.c_uint64), ("lift_inv_off", ctypes.c_uint64),
+                ("units_off", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I = ctypes.c_int
@@ -69,7 +77,8 @@ _SIGNATURES = {
     "wp_wpinv_workspace": ([_I64, _I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wpinv": ([_P, _P, _I64, _I64, _I64, _I, ctypes.c_double, _I, _P, _SZ, _P], _I),
     "wp_batched_workspace": ([ctypes.POINTER(WPBatchItem), _I, ctypes.POINTER(_SZ)], _I),
-    "wp_batched": ([ctypes.POINTER(WPBatchItem), _I, _P, _SZ, _P], _I),
+    "wp_batched_plan": ([ctypes.POINTER(WPBatchItem), _I, _I, _P, _SZ, ctypes.POINTER(WPBatchPlan), _P], _I),
+    "wp_batched_run": ([ctypes.POINTER(WPBatchPlan), _P, _P], _I),
 }
 
 
@@ -282,6 +291,35 @@ def wp_wpinv(A, L, rtol=-1.0, refine_iters=0, ws=None):
     _check(lib().wp_wpinv(_ptr(A), _ptr(X), m, n, p, L, float(rtol), int(refine_iters), _ptr(ws), ws.numel(),
                           _stream()), "wp_wpinv")
     return X
+
+
+# ---- batched launch -----------------------------------------------------------------
+
+class BatchedLaunch:
+    """w-product + rank-r w-svd over many uneven items (wp_batched_plan /
+    wp_batched_run).  `items`: list of dicts with CUDA tensors A, B, C, C_r
+    and ints L, r.  run() only launches, so it may be captured in a CUDA graph."""
+
+    def __init__(self, items, tune=False):
+        arr = (WPBatchItem * len(items))()
+        for i, it in enumerate(items):
+            A, B, C, Cr = it["A"], it["B"], it["C"], it["C_r"]
+            for t, nm in ((A, "A"), (B, "B"), (C, "C"), (Cr, "C_r")):
+                _req(t, nm)
+            p, n1, n2 = A.shape
+            arr[i] = WPBatchItem(A.data_ptr(), B.data_ptr(), C.data_ptr(), Cr.data_ptr(), n1, n2, B.shape[2], p,
+                                 int(it["L"]), int(it["r"]))
+        self._arr = arr
+        self._keep = items
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().wp_batched_workspace(arr, len(items), ctypes.byref(nbytes)), "wp_batched_workspace")
+        self.ws = _workspace(nbytes.value, items[0]["A"].device)
+        self.plan = WPBatchPlan()
+        _check(lib().wp_batched_plan(arr, len(items), int(bool(tune)), _ptr(self.ws), self.ws.numel(),
+                                     ctypes.byref(self.plan), _stream()), "wp_batched_plan")
+
+    def run(self):
+        _check(lib().wp_batched_run(ctypes.byref(self.plan), _ptr(self.ws), _stream()), "wp_batched_run")
 
 
 def wp_profile_begin():

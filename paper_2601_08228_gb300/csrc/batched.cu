@@ -1,5 +1,479 @@
-// Batched launch over many uneven tensors (placeholder until the persistent kernel lands).
-#include "common.cuh"
+// Batched launch over many uneven tensors: for every item, C = A *w B
+// (Def. 2.1, Algorithm 1) and C_r = rank-r w-svd of A (Algorithm 2).
+//
+// The host builds the work lists once (wp_batched_plan) into the workspace;
+// wp_batched_run then issues four persistent, grouped kernels whose CTAs loop
+// over those lists, so one launch covers every item of a phase whatever its
+// shape:
+//   1. lifting      every A and B (one descriptor per tensor, CTA-sized
+//                   chunks of (tube group, plane range), L dispatched per chunk)
+//   2. face-product every wavelet-domain slice A_hat_k B_hat_k (one slice per
+//                   CTA iteration, operands staged in shared memory)
+//   3. Jacobi SVD   every slice of A_hat (one-sided Jacobi in shared memory),
+//                   the rank-r slice C_hat_k = U_r U_r^T A_hat_k (or
+//                   A_hat_k V_r V_r^T) rebuilt in the same CTA
+//   4. inverse lifting of every C_hat and C_hat_r
+// wp_batched_run performs no allocation, host synchronisation or copy, so it
+// can be captured in a CUDA graph.  The CTA sizes of phases 2 and 3 are picked
+// by timing candidates on the planned work (wp_batched_plan with tune = 1).
 
-extern "C" int wp_batched_workspace(const wp_batch_item*, int, size_t*) { return WP_ERR_UNSUPPORTED; }
-extern "C" int wp_batched(const wp_batch_item*, int, void*, size_t, void*) { return WP_ERR_UNSUPPORTED; }
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "lift_math.cuh"
+
+namespace wp {
+
+struct BItem {
+  const float* A;
+  const float* B;
+  float* C;
+  float* Cr;
+  float* Ah;    // workspace: wavelet-domain A, B, C, C_r
+  float* Bh;
+  float* Ch;
+  float* Crh;
+  int n1, n2, n4, p, L, r;
+};
+
+struct LiftDesc {
+  const float* src;
+  float* dst;
+  int64_t first_block;   // first CTA-chunk index of this tensor
+  int32_t plane, p, L, op;
+  int32_t chunks_per_group;
+};
+
+constexpr int BL_THREADS = 256;
+
+// ---- phase 1 / 4: grouped lifting ---------------------------------------------------
+
+template <int L>
+__device__ __forceinline__ void lift_chunk(const LiftDesc& d, int64_t g, int64_t e) {
+  constexpr int G = 1 << L;
+  float x[G], y[G];
+  const bool fwd = (d.op == LIFT_FWD);
+#pragma unroll
+  for (int t = 0; t < G; ++t) {
+    const int64_t slice = fwd ? g * G + t : mallat_slice<L>(t, g, d.p);
+    x[t] = __ldg(d.src + slice * d.plane + e);
+  }
+  if (fwd) lift_group<L>(x, y);
+  else ilift_group<L>(x, y);
+#pragma unroll
+  for (int t = 0; t < G; ++t) {
+    const int64_t slice = fwd ? mallat_slice<L>(t, g, d.p) : g * G + t;
+    d.dst[slice * d.plane + e] = y[t];
+  }
+}
+
+__global__ void __launch_bounds__(BL_THREADS) batched_lift_kernel(const LiftDesc* __restrict__ descs, int ndesc,
+                                                                  int64_t total_blocks) {
+  for (int64_t b = blockIdx.x; b < total_blocks; b += gridDim.x) {
+    // binary search for the descriptor owning CTA-chunk b
+    int lo = 0, hi = ndesc - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (descs[mid].first_block <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const LiftDesc d = descs[lo];
+    const int64_t local = b - d.first_block;
+    const int64_t g = local / d.chunks_per_group;
+    const int64_t e = (local % d.chunks_per_group) * BL_THREADS + threadIdx.x;
+    if (e >= d.plane) continue;
+    switch (d.L) {
+      case 0: lift_chunk<0>(d, g, e); break;
+      case 1: lift_chunk<1>(d, g, e); break;
+      case 2: lift_chunk<2>(d, g, e); break;
+      case 3: lift_chunk<3>(d, g, e); break;
+      case 4: lift_chunk<4>(d, g, e); break;
+      default: lift_chunk<5>(d, g, e); break;
+    }
+  }
+}
+
+// ---- phase 2: grouped face-products (n1, n2, n4 <= 64) --------------------------------
+
+constexpr int BMAX = 64;
+
+__global__ void batched_facewise_kernel(const BItem* __restrict__ items, const int2* __restrict__ units,
+                                        int64_t nunits) {
+  __shared__ float As[BMAX][BMAX + 1];
+  __shared__ float Bs[BMAX][BMAX + 1];
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int2 uk = units[u];
+    const BItem it = items[uk.x];
+    const int n1 = it.n1, n2 = it.n2, n4 = it.n4;
+    const float* a = it.Ah + int64_t(uk.y) * n1 * n2;
+    const float* bm = it.Bh + int64_t(uk.y) * n2 * n4;
+    float* c = it.Ch + int64_t(uk.y) * n1 * n4;
+    for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) As[i / n2][i % n2] = a[i];
+    for (int i = threadIdx.x; i < n2 * n4; i += blockDim.x) Bs[i / n4][i % n4] = bm[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1 * n4; i += blockDim.x) {
+      const int row = i / n4, col = i % n4;
+      float acc = 0.f;
+      for (int k = 0; k < n2; ++k) acc = fmaf(As[row][k], Bs[k][col], acc);
+      c[i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- phase 3: grouped Jacobi SVD + rank-r rebuild ---------------------------------------
+
+__device__ __forceinline__ void circle_pair(int i, int k, int n, int& a, int& b) {
+  auto elem = [&](int pos) {
+    int q = pos - 1 + k;
+    q -= (q >= n - 1) ? (n - 1) : 0;
+    return pos == 0 ? 0 : 1 + q;
+  };
+  a = elem(i);
+  b = elem(n - 1 - i);
+}
+
+// shared memory layout per CTA: Xs [64][64] (column-major, stride m_len),
+// reused for T once the leading vectors are extracted; vec [64][64]
+// (m_len x r); norms [64]
+constexpr int JB_SMEM_FLOATS = BMAX * BMAX * 2 + BMAX;
+
+__global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int2* __restrict__ units,
+                                      int64_t nunits, int max_sweeps, int* status) {
+  __shared__ float sm[JB_SMEM_FLOATS];
+  __shared__ int order[BMAX];
+  float* Xs = sm;
+  float* vec = sm + BMAX * BMAX;
+  float* T = Xs;                       // after vec is built, Xs is free
+  float* norms = vec + BMAX * BMAX;
+  const int nthr = blockDim.x, nwarps = nthr >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int2 uk = units[u];
+    const BItem it = items[uk.x];
+    const int n1 = it.n1, n2 = it.n2, r = it.r;
+    const bool trans = n1 < n2;
+    const int m_len = trans ? n2 : n1, n_vec = trans ? n1 : n2;
+    const int n_pad = std::max(2, n_vec + (n_vec & 1));
+    const int npairs = n_pad / 2;
+    const float* A = it.Ah + int64_t(uk.y) * n1 * n2;
+    const float tol = 2.f * sqrtf(float(max(m_len, 16))) * 1.1920929e-7f;
+    for (int idx = threadIdx.x; idx < n_pad * m_len; idx += nthr) {
+      const int c = idx / m_len, R = idx % m_len;
+      Xs[idx] = (c < n_vec) ? (trans ? A[c * n2 + R] : A[R * n2 + c]) : 0.f;
+    }
+    __syncthreads();
+    bool converged = false;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      for (int c = warp; c < n_pad; c += nwarps) {
+        float s = 0.f;
+        for (int R = lane; R < m_len; R += 32) s = fmaf(Xs[c * m_len + R], Xs[c * m_len + R], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) norms[c] = s;
+      }
+      __syncthreads();
+      int rotated_sweep = 0;
+      for (int k = 0; k < n_pad - 1; ++k) {
+        int rotated = 0;
+        for (int i = warp; i < npairs; i += nwarps) {
+          int ca, cb;
+          circle_pair(i, k, n_pad, ca, cb);
+          float* xa = Xs + ca * m_len;
+          float* xb = Xs + cb * m_len;
+          // m_len <= 64: two rows per lane, kept in registers
+          const int r0 = lane, r1 = lane + 32;
+          const float u0 = r0 < m_len ? xa[r0] : 0.f, v0 = r0 < m_len ? xb[r0] : 0.f;
+          const float u1 = r1 < m_len ? xa[r1] : 0.f, v1 = r1 < m_len ? xb[r1] : 0.f;
+          float g = fmaf(u0, v0, u1 * v1);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+          const float al = norms[ca], be = norms[cb];
+          if (g != 0.f && fabsf(g) > tol * sqrtf(al * be)) {
+            const float zeta = __fdividef(be - al, 2.f * g);
+            const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            const float cs = rsqrtf(fmaf(t, t, 1.f));
+            const float sn = cs * t;
+            if (r0 < m_len) { xa[r0] = fmaf(cs, u0, -sn * v0); xb[r0] = fmaf(sn, u0, cs * v0); }
+            if (r1 < m_len) { xa[r1] = fmaf(cs, u1, -sn * v1); xb[r1] = fmaf(sn, u1, cs * v1); }
+            __syncwarp();
+            if (lane == 0) { norms[ca] = fmaf(-t, g, al); norms[cb] = fmaf(t, g, be); }
+            rotated = 1;
+          }
+        }
+        rotated_sweep |= __syncthreads_or(rotated);
+      }
+      if (!rotated_sweep) { converged = true; break; }
+    }
+    if (!converged && threadIdx.x == 0) report_device_error(status, WP_ERR_NOT_CONVERGED);
+    // exact norms, rank the columns, normalised leading vectors into vec (m_len x r)
+    for (int c = warp; c < n_pad; c += nwarps) {
+      float s = 0.f;
+      for (int R = lane; R < m_len; R += 32) s = fmaf(Xs[c * m_len + R], Xs[c * m_len + R], s);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) norms[c] = s;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_vec; c += nthr) {
+      const float sc = norms[c];
+      int pos = 0;
+      for (int q = 0; q < n_vec; ++q) pos += (norms[q] > sc) || (norms[q] == sc && q < c);
+      if (pos < r) order[pos] = c;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < m_len * r; idx += nthr) {
+      const int R = idx / r, kq = idx % r;
+      const int c = order[kq];
+      const float sg = sqrtf(norms[c]);
+      vec[idx] = sg > 0.f ? Xs[c * m_len + R] / sg : 0.f;
+    }
+    __syncthreads();
+    // rebuild the rank-r slice from the original A_hat_k (still in global memory)
+    float* Cr = it.Crh + int64_t(uk.y) * n1 * n2;
+    if (!trans) {
+      // T = U^T A (r x n2), C = U T
+      for (int idx = threadIdx.x; idx < r * n2; idx += nthr) {
+        const int kq = idx / n2, j = idx % n2;
+        float acc = 0.f;
+        for (int i = 0; i < n1; ++i) acc = fmaf(vec[i * r + kq], A[i * n2 + j], acc);
+        T[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < n1 * n2; idx += nthr) {
+        const int i = idx / n2, j = idx % n2;
+        float acc = 0.f;
+        for (int kq = 0; kq < r; ++kq) acc = fmaf(vec[i * r + kq], T[kq * n2 + j], acc);
+        Cr[idx] = acc;
+      }
+    } else {
+      // T = A V (n1 x r), C = T V^T
+      for (int idx = threadIdx.x; idx < n1 * r; idx += nthr) {
+        const int i = idx / r, kq = idx % r;
+        float acc = 0.f;
+        for (int j = 0; j < n2; ++j) acc = fmaf(A[i * n2 + j], vec[j * r + kq], acc);
+        T[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < n1 * n2; idx += nthr) {
+        const int i = idx / n2, j = idx % n2;
+        float acc = 0.f;
+        for (int kq = 0; kq < r; ++kq) acc = fmaf(T[i * r + kq], vec[j * r + kq], acc);
+        Cr[idx] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- host side --------------------------------------------------------------------------------
+
+static int validate_items(const wp_batch_item* items, int count) {
+  if (!items) return WP_ERR_NULL;
+  if (count < 1) return WP_ERR_SHAPE;
+  for (int i = 0; i < count; ++i) {
+    const wp_batch_item& t = items[i];
+    if (t.n1 < 1 || t.n2 < 1 || t.n4 < 1 || t.p < 1 || t.n1 > BMAX || t.n2 > BMAX || t.n4 > BMAX)
+      return WP_ERR_SHAPE;
+    if (t.L < 0 || t.L > 5 || (t.p % (1 << t.L)) != 0) return WP_ERR_LEVELS;
+    if (t.r < 1 || t.r > std::min(t.n1, t.n2)) return WP_ERR_RANK;
+    if (!t.A || !t.B || !t.C || !t.C_r) return WP_ERR_NULL;
+    if (!aligned16(t.A) || !aligned16(t.B) || !aligned16(t.C) || !aligned16(t.C_r)) return WP_ERR_ALIGN;
+  }
+  return WP_OK;
+}
+
+struct BatchLayout {
+  size_t items_off, lift1_off, lift2_off, units_off, data_off, total;
+  int64_t nunits;
+  std::vector<size_t> tensor_off;   // per item: offset (floats) of Ah inside the data region
+};
+
+static void batch_layout(const wp_batch_item* items, int count, BatchLayout& lay) {
+  Sizer s;
+  lay.items_off = 0;
+  s.take<BItem>(count);
+  lay.lift1_off = s.bytes();
+  s.take<LiftDesc>(2 * size_t(count));
+  lay.lift2_off = s.bytes();
+  s.take<LiftDesc>(2 * size_t(count));
+  lay.units_off = s.bytes();
+  lay.nunits = 0;
+  for (int i = 0; i < count; ++i) lay.nunits += items[i].p;
+  s.take<int2>(size_t(lay.nunits));
+  lay.data_off = s.bytes();
+  size_t floats = 0;
+  lay.tensor_off.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const wp_batch_item& t = items[i];
+    lay.tensor_off[i] = floats;
+    const size_t p = size_t(t.p);
+    floats += p * t.n1 * t.n2;        // A_hat
+    floats = align_up(floats, 64);
+    floats += p * t.n2 * t.n4;        // B_hat
+    floats = align_up(floats, 64);
+    floats += p * t.n1 * t.n4;        // C_hat
+    floats = align_up(floats, 64);
+    floats += p * t.n1 * t.n2;        // C_hat_r
+    floats = align_up(floats, 64);
+  }
+  lay.total = lay.data_off + floats * sizeof(float);
+}
+
+static int64_t make_lift_descs(std::vector<LiftDesc>& d, const float* src, float* dst, int plane, int p, int L,
+                               int op, int64_t first) {
+  LiftDesc x{};
+  x.src = src;
+  x.dst = dst;
+  x.first_block = first;
+  x.plane = plane;
+  x.p = p;
+  x.L = L;
+  x.op = op;
+  x.chunks_per_group = (plane + BL_THREADS - 1) / BL_THREADS;
+  d.push_back(x);
+  return first + int64_t(p >> L) * x.chunks_per_group;
+}
+
+static int launch_batched_lift(const LiftDesc* d, int ndesc, int64_t blocks, cudaStream_t st) {
+  const int64_t grid = std::min<int64_t>(blocks, int64_t(sm_count()) * 8);
+  WP_PROFILE("batched_lift", st);
+  batched_lift_kernel<<<unsigned(std::max<int64_t>(grid, 1)), BL_THREADS, 0, st>>>(d, ndesc, blocks);
+  return launch_status();
+}
+
+static int launch_batched_gemm(const BItem* items, const int2* units, int64_t n, int threads, cudaStream_t st) {
+  const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * (2048 / threads));
+  WP_PROFILE("batched_facewise", st);
+  batched_facewise_kernel<<<unsigned(std::max<int64_t>(grid, 1)), threads, 0, st>>>(items, units, n);
+  return launch_status();
+}
+
+static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t n, int threads, cudaStream_t st) {
+  const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * (2048 / threads));
+  WP_PROFILE("batched_jacobi", st);
+  batched_jacobi_kernel<<<unsigned(std::max<int64_t>(grid, 1)), threads, 0, st>>>(items, units, n, 40,
+                                                                                  device_status_ptr());
+  return launch_status();
+}
+
+// Time one candidate configuration of a phase (median of 3 runs).
+template <typename F>
+static float time_candidate(F&& fn, cudaStream_t st) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(a, st);
+    fn();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+}  // namespace wp
+
+using namespace wp;
+
+extern "C" int wp_batched_workspace(const wp_batch_item* items, int count, size_t* bytes) {
+  if (!bytes) return WP_ERR_NULL;
+  WP_TRY(validate_items(items, count));
+  BatchLayout lay;
+  batch_layout(items, count, lay);
+  *bytes = lay.total;
+  return WP_OK;
+}
+
+extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, void* ws, size_t ws_bytes,
+                               wp_batch_plan* plan, void* stream) {
+  if (!plan) return WP_ERR_NULL;
+  WP_TRY(validate_items(items, count));
+  BatchLayout lay;
+  batch_layout(items, count, lay);
+  if (!ws || ws_bytes < lay.total) return WP_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
+  char* base = static_cast<char*>(ws);
+  float* data = reinterpret_cast<float*>(base + lay.data_off);
+  std::vector<BItem> bi(count);
+  std::vector<LiftDesc> l1, l2;
+  std::vector<int2> units;
+  units.reserve(size_t(lay.nunits));
+  int64_t b1 = 0, b2 = 0;
+  for (int i = 0; i < count; ++i) {
+    const wp_batch_item& t = items[i];
+    BItem& x = bi[i];
+    x.A = t.A; x.B = t.B; x.C = t.C; x.Cr = t.C_r;
+    size_t off = lay.tensor_off[i];
+    const size_t p = size_t(t.p);
+    x.Ah = data + off; off = align_up(off + p * t.n1 * t.n2, 64);
+    x.Bh = data + off; off = align_up(off + p * t.n2 * t.n4, 64);
+    x.Ch = data + off; off = align_up(off + p * t.n1 * t.n4, 64);
+    x.Crh = data + off;
+    x.n1 = t.n1; x.n2 = t.n2; x.n4 = t.n4; x.p = t.p; x.L = t.L; x.r = t.r;
+    b1 = make_lift_descs(l1, t.A, x.Ah, t.n1 * t.n2, t.p, t.L, LIFT_FWD, b1);
+    b1 = make_lift_descs(l1, t.B, x.Bh, t.n2 * t.n4, t.p, t.L, LIFT_FWD, b1);
+    b2 = make_lift_descs(l2, x.Ch, t.C, t.n1 * t.n4, t.p, t.L, LIFT_INV, b2);
+    b2 = make_lift_descs(l2, x.Crh, t.C_r, t.n1 * t.n2, t.p, t.L, LIFT_INV, b2);
+    for (int k = 0; k < t.p; ++k) units.push_back(make_int2(i, k));
+  }
+  cudaStream_t st = as_stream(stream);
+  WP_CUDA_TRY(cudaMemcpyAsync(base + lay.items_off, bi.data(), bi.size() * sizeof(BItem), cudaMemcpyHostToDevice, st));
+  WP_CUDA_TRY(cudaMemcpyAsync(base + lay.lift1_off, l1.data(), l1.size() * sizeof(LiftDesc), cudaMemcpyHostToDevice, st));
+  WP_CUDA_TRY(cudaMemcpyAsync(base + lay.lift2_off, l2.data(), l2.size() * sizeof(LiftDesc), cudaMemcpyHostToDevice, st));
+  WP_CUDA_TRY(cudaMemcpyAsync(base + lay.units_off, units.data(), units.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  WP_CUDA_TRY(cudaStreamSynchronize(st));   // host vectors go out of scope below
+  plan->count = count;
+  plan->items_off = lay.items_off;
+  plan->lift_fwd_off = lay.lift1_off;
+  plan->lift_inv_off = lay.lift2_off;
+  plan->units_off = lay.units_off;
+  plan->n_lift_fwd = int32_t(l1.size());
+  plan->n_lift_inv = int32_t(l2.size());
+  plan->lift_fwd_blocks = b1;
+  plan->lift_inv_blocks = b2;
+  plan->n_units = lay.nunits;
+  plan->gemm_threads = 256;
+  plan->svd_threads = 128;
+  if (tune) {
+    // autotune the CTA sizes of the face-product and Jacobi phases on the
+    // planned work (phase 1 first so that the operands are real)
+    const BItem* di = reinterpret_cast<const BItem*>(base + lay.items_off);
+    const int2* du = reinterpret_cast<const int2*>(base + lay.units_off);
+    WP_TRY(launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + lay.lift1_off), plan->n_lift_fwd, b1, st));
+    float best = 1e30f;
+    for (int thr : {64, 128, 256, 512}) {
+      const float t = time_candidate([&] { launch_batched_gemm(di, du, lay.nunits, thr, st); }, st);
+      if (t < best) { best = t; plan->gemm_threads = thr; }
+    }
+    best = 1e30f;
+    for (int thr : {64, 128, 256}) {
+      const float t = time_candidate([&] { launch_batched_jacobi(di, du, lay.nunits, thr, st); }, st);
+      if (t < best) { best = t; plan->svd_threads = thr; }
+    }
+    WP_CUDA_TRY(cudaGetLastError());
+  }
+  return WP_OK;
+}
+
+extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream) {
+  if (!plan || !ws) return WP_ERR_NULL;
+  if (plan->count < 1 || plan->n_units < 1) return WP_ERR_SHAPE;
+  char* base = static_cast<char*>(ws);
+  cudaStream_t st = as_stream(stream);
+  const BItem* di = reinterpret_cast<const BItem*>(base + plan->items_off);
+  const int2* du = reinterpret_cast<const int2*>(base + plan->units_off);
+  WP_TRY(launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_fwd_off), plan->n_lift_fwd,
+                             plan->lift_fwd_blocks, st));
+  WP_TRY(launch_batched_gemm(di, du, plan->n_units, plan->gemm_threads, st));
+  WP_TRY(launch_batched_jacobi(di, du, plan->n_units, plan->svd_threads, st));
+  return launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_inv_off), plan->n_lift_inv,
+                             plan->lift_inv_blocks, st);
+}
