@@ -52,6 +52,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", default="bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-launch and deblurring measurements")
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "jacobi", "batched"], default=None,
+                    help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
 
 
@@ -156,15 +160,23 @@ def _src_hash(fname):
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when it is absent or the kernel's source changed since."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes (read + write) per launch of `kernel` at this workload, from
+    the table in profiles/ncu_traffic.md, or None when the entry is absent or
+    the kernel's source file changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path)).get(kernel)
-    if not d or _src_hash(d.get("source", "")) != d.get("source_sha"):
-        return None
-    return d.get("dram_bytes_per_launch")
+    for line in open(path):
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel:
+            src, sha, val = cells[1], cells[2], cells[3]
+            if _src_hash(src) != sha:
+                return None
+            try:
+                return float(val)
+            except ValueError:
+                return None
+    return None
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -284,6 +296,7 @@ def run_ours(args):
         dist.barrier()
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     launches0 = capi.wp_launch_count()
+    capi.wp_jacobi_stats()          # clear the sweep counters
     with ClockSampler(local) as clk:
         capi.wp_profile_begin()
         torch.cuda.synchronize()
@@ -293,6 +306,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         prof = capi.wp_profile_end()
     launches = capi.wp_launch_count() - launches0
+    tot_sw, max_sw = capi.wp_jacobi_stats()
+    jac = {"total_sweeps": tot_sw, "max_sweeps": max_sw}
     t_prod = sum(e[0].elapsed_time(e[1]) for e in events) / 1e3
     t_wsvd = sum(e[1].elapsed_time(e[2]) for e in events) / 1e3 if have_wsvd else 0.0
     t_sp = sum(e[2].elapsed_time(e[3]) for e in events) / 1e3 if have_wsvd else 0.0
@@ -322,7 +337,7 @@ def run_ours(args):
     clocks = clk.summary()
     peaks = measured_peaks()
     sm = torch.cuda.get_device_properties(local).multi_processor_count
-    roof = _roofline(prof, peaks, sm, args.steps, have_wsvd)
+    roof = _roofline(prof, peaks, sm, args.steps, have_wsvd, jac)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step / args.steps, "higher_is_better": True,
@@ -338,10 +353,13 @@ def run_ours(args):
         "rel_err": {"mixed": err_mixed, "fp32": err_fp32},
         "roofline": roof,
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "jacobi_sweeps": jac,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,
     }
+    if not args.no_extras:
+        line["extras"] = _extras(capi, args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     print(json.dumps(line), flush=True)
@@ -408,7 +426,7 @@ def _e2e(capi, A_h, B_h, L, prec, warmup, steps):
             "h2d_bytes_per_step": Ap.numel() * 4 + Bp.numel() * 4, "d2h_bytes_per_step": Cp.numel() * 4}
 
 
-def _roofline(prof, peaks, sm_count, steps, have_wsvd):
+def _roofline(prof, peaks, sm_count, steps, have_wsvd, jac=None):
     """Roofline entry for the kernel with the largest share of the step."""
     if not prof:
         return None
@@ -438,12 +456,117 @@ def _roofline(prof, peaks, sm_count, steps, have_wsvd):
         peak = peaks["bf16_tflops_sustained"]
         return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": ncu_traffic(name), "peak_source": peaks["source"] + " bf16 sustained"}
+    if name == "jacobi_svd" and jac is not None:
+        # algorithmic flops: per sweep of one slice, (n-1) rounds x n/2 pairs x
+        # m rows x 8 (dot product 2, plane rotation 6) plus 2 m n for the norms
+        n, m = w["n2"], w["n1"]
+        per_sweep = (n - 1) * (n // 2) * m * 8 + 2 * m * n
+        flops = jac["total_sweeps"] * per_sweep
+        ach = flops / (ms / 1e3) / 1e12
+        peak = fp32_simt_peak_tflops(sm_count, peaks["sm_max_mhz"])
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": ncu_traffic(name),
+                "peak_source": f"FP32 SIMT 2*128*{sm_count} SMs*{peaks['sm_max_mhz']:.0f} MHz",
+                "work": f"{jac['total_sweeps']} slice-sweeps x {per_sweep} flops"}
     return {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": ncu_traffic(name), "avg_launch_ms": avg_s * 1e3}
 
 
+def _extras(capi, args):
+    """Two further workloads timed with the same event protocol: the batched
+    launch over 4096 uneven items (w-product + rank-8 w-svd per item, one
+    CUDA graph) and one 512x512x128 deblurring gradient step (BF16x3)."""
+    import torch
+    import oracle as O
+    from paper_2601_08228_gb300 import synth
+    out = {}
+    items = synth.batch_items(count=4096, seed=1)
+    dev = []
+    for it in items:
+        A = torch.from_numpy(it["A"]).cuda()
+        dev.append(dict(A=A, B=torch.from_numpy(it["B"]).cuda(),
+                        C=torch.empty((it["p"], it["n1"], it["n4"]), device="cuda"), C_r=torch.empty_like(A),
+                        L=it["L"], r=8))
+    bl = capi.BatchedLaunch(dev, tune=True)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            bl.run()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    a.record()
+    for _ in range(reps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3 / reps
+    out["batched_4096"] = {"tensors_per_s": 4096 / t, "ms": t * 1e3, "graph": True,
+                           "gemm_threads": bl.plan.gemm_threads, "svd_threads": bl.plan.svd_threads}
+    del dev, bl, g
+    # deblurring step at 512 x 512 x 128, L = 4
+    n, p, L = 512, 128, 4
+    K = synth.blur_operator(n, p, dtype=np.float32)
+    Xt = synth.hsi_cube(n, n, p, rank=8, noise=0.0, seed=2, dtype=np.float32)
+    Y = O.wprod(K, Xt, L)
+    Y = (Y + 0.01 * Y.std() * synth.unit_noise(Y.shape, 3)).astype(np.float32)
+    Kd, Yd = torch.from_numpy(K).cuda(), torch.from_numpy(Y).cuda()
+    X = torch.zeros_like(Yd)
+    ws = torch.empty(capi.wp_deblur_workspace(n, n, p, L, "bf16x3"), dtype=torch.uint8, device="cuda")
+    eta = 1.0 / (2.0 * (1.0 + 1e-3))
+    for _ in range(3):
+        capi.wp_deblur_step(Kd, Yd, X, L, 1e-3, eta, prec="bf16x3", ws=ws)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(10):
+        capi.wp_deblur_step(Kd, Yd, X, L, 1e-3, eta, prec="bf16x3", ws=ws)
+    b.record()
+    torch.cuda.synchronize()
+    step = a.elapsed_time(b) / 10
+    out["deblur_512x512x128"] = {"ms_per_step": step, "ms_200_steps": 200 * step,
+                                 "tflops": 2 * 2 * n ** 3 * p / (step / 1e3) / 1e12, "prec": "bf16x3"}
+    return out
+
+
+def run_profile_case(case):
+    """One small invocation of one kernel family, for ncu captures (inputs
+    larger than L2 where DRAM counters matter, a few GB at most)."""
+    import torch
+    from paper_2601_08228_gb300 import capi, synth
+    capi.lib()
+    if case == "lift":
+        x = torch.rand((768, 256, 256), device="cuda")      # 201 MB > L2
+        capi.wp_lift_forward(x, 3)
+    elif case == "gemm":
+        A = torch.rand((192, 256, 256), device="cuda")
+        B = torch.rand((192, 256, 256), device="cuda")
+        capi.wp_facewise(A, B, prec="bf16x3")
+    elif case == "jacobi":
+        A = torch.from_numpy(synth.hsi_cube(256, 256, 16, seed=0, dtype=np.float32)).cuda()
+        capi.wp_wsvd(A, 3, 20)
+    elif case == "batched":
+        items = synth.batch_items(count=64, seed=1)
+        dev = []
+        for it in items:
+            A = torch.from_numpy(it["A"]).cuda()
+            dev.append(dict(A=A, B=torch.from_numpy(it["B"]).cuda(),
+                            C=torch.empty((it["p"], it["n1"], it["n4"]), device="cuda"), C_r=torch.empty_like(A),
+                            L=it["L"], r=8))
+        capi.BatchedLaunch(dev).run()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "ok": True}))
+
+
 def main():
     args = parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

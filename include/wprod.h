@@ -103,6 +103,11 @@ WP_API int wp_profile_count(void);
 WP_API int wp_profile_get(int index, char* name, int name_len, int64_t* launches,
                           double* total_ms);
 
+/* Jacobi SVD counters since the last call (synchronises the device, then
+ * clears them): the sum over slices of the sweeps each needed, and the
+ * largest sweep count of any slice. */
+WP_API int wp_jacobi_stats(int64_t* total_sweeps, int* max_sweeps);
+
 /* Synchronise `stream`, then return and clear the device status word of the
  * current device (WP_OK if no kernel reported a fault since the last call).
  * Returns WP_ERR_CUDA if the synchronisation itself fails. */

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "wp_version": ([], _I),
     "wp_launch_count": ([], ctypes.c_uint64),
     "wp_get_device_error": ([_P], _I),
+    "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
     "wp_profile_begin": ([], _I),
     "wp_profile_end": ([], _I),
     "wp_profile_count": ([], _I),
@@ -336,6 +337,13 @@ def wp_profile_end():
         _check(lib().wp_profile_get(i, buf, 128, ctypes.byref(n), ctypes.byref(ms)), "wp_profile_get")
         out[buf.value.decode()] = (int(n.value), float(ms.value))
     return out
+
+
+def wp_jacobi_stats():
+    """(total slice-sweeps, max sweeps of one slice) since the last call."""
+    t, m = _I64(0), _I(0)
+    _check(lib().wp_jacobi_stats(ctypes.byref(t), ctypes.byref(m)), "wp_jacobi_stats")
+    return int(t.value), int(m.value)
 
 
 def wp_launch_count():

@@ -140,7 +140,8 @@ __device__ __forceinline__ void circle_pair(int i, int k, int n, int& a, int& b)
 constexpr int JB_SMEM_FLOATS = BMAX * BMAX * 2 + BMAX;
 
 __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int2* __restrict__ units,
-                                      int64_t nunits, int max_sweeps, int* status) {
+                                      int64_t nunits, int max_sweeps, int* status,
+                                      unsigned long long* stats) {
   __shared__ float sm[JB_SMEM_FLOATS];
   __shared__ int order[BMAX];
   float* Xs = sm;
@@ -165,7 +166,10 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
     }
     __syncthreads();
     bool converged = false;
+    int sweeps_done = 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+      sweeps_done = sweep + 1;
+      const float tol_eff = sweep < 20 ? tol : 8.f * tol;   // see jacobi.cu
       for (int c = warp; c < n_pad; c += nwarps) {
         float s = 0.f;
         for (int R = lane; R < m_len; R += 32) s = fmaf(Xs[c * m_len + R], Xs[c * m_len + R], s);
@@ -190,7 +194,7 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
           const float al = norms[ca], be = norms[cb];
-          if (g != 0.f && fabsf(g) > tol * sqrtf(al * be)) {
+          if (g != 0.f && fabsf(g) > tol_eff * sqrtf(al * be)) {
             const float zeta = __fdividef(be - al, 2.f * g);
             const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             const float cs = rsqrtf(fmaf(t, t, 1.f));
@@ -207,6 +211,10 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
       if (!rotated_sweep) { converged = true; break; }
     }
     if (!converged && threadIdx.x == 0) report_device_error(status, WP_ERR_NOT_CONVERGED);
+    if (threadIdx.x == 0 && stats) {
+      atomicAdd(&stats[0], (unsigned long long)sweeps_done);
+      atomicMax(&stats[1], (unsigned long long)sweeps_done);
+    }
     // exact norms, rank the columns, normalised leading vectors into vec (m_len x r)
     for (int c = warp; c < n_pad; c += nwarps) {
       float s = 0.f;
@@ -354,7 +362,8 @@ static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t 
   const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * (2048 / threads));
   WP_PROFILE("batched_jacobi", st);
   batched_jacobi_kernel<<<unsigned(std::max<int64_t>(grid, 1)), threads, 0, st>>>(items, units, n, 40,
-                                                                                  device_status_ptr());
+                                                                                  device_status_ptr(),
+                                                                                  jacobi_stats_ptr());
   return launch_status();
 }
 

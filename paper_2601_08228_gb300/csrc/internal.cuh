@@ -33,5 +33,7 @@ namespace wp {
 int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, float* vec_out, float* sig_out,
                cudaStream_t st);
 bool jacobi_supported(int n1, int n2);
+// Device address of the Jacobi sweep counters ([0] total slice-sweeps, [1] max).
+unsigned long long* jacobi_stats_ptr();
 
 }  // namespace wp

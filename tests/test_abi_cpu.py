@@ -26,7 +26,7 @@ def _declared_symbols():
 
 def test_exports_every_declared_symbol(libwprod):
     names = _declared_symbols()
-    assert len(names) >= 27
+    assert len(names) >= 28
     for n in names:
         assert hasattr(libwprod, n), n
 

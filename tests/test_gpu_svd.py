@@ -87,6 +87,7 @@ def test_wsvd_parity(p, n1, n2, L, r, sparse):
     Ch_gpu = np.einsum("kir,kr,kjr->kij", U, S, V)
     Ch_ref = np.einsum("kir,kr,kjr->kij", Ur, Sr, Vr)
     assert O.rel_fro(Ch_gpu, Ch_ref) <= tol_rec
+    assert capi.wp_get_device_error() == 0
     eye = np.broadcast_to(np.eye(r), (nsl, r, r))
     assert np.max(np.abs(np.einsum("kir,kis->krs", U[:nsl], U[:nsl]) - eye)) <= 1e-5 * max(n1, n2)
     assert np.max(np.abs(np.einsum("kir,kis->krs", V[:nsl], V[:nsl]) - eye)) <= 1e-5 * max(n1, n2)
@@ -169,6 +170,7 @@ def test_wpinv_parity_and_penrose(p, m, n, L, refine):
     assert O.rel_fro(O.wprod(XA, X, L), X) <= tol_pen
     assert O.rel_fro(O.transpose(AX), AX) <= tol_pen
     assert O.rel_fro(O.transpose(XA), XA) <= tol_pen
+    assert capi.wp_get_device_error() == 0
 
 
 def test_wpinv_refinement_reduces_error():
@@ -182,6 +184,7 @@ def test_wpinv_refinement_reduces_error():
     e0 = O.rel_fro(host(capi.wp_wpinv(dev(A), L, refine_iters=0)), ref)
     e2 = O.rel_fro(host(capi.wp_wpinv(dev(A), L, refine_iters=2)), ref)
     assert e2 <= e0 and e2 <= 1e-3
+    assert capi.wp_get_device_error() == 0
 
 
 def test_wpinv_invertible_gives_identity():
