@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
-    ap.add_argument("--profile-case", choices=["lift", "gemm", "jacobi", "batched"], default=None,
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "wprod", "jacobi", "batched"], default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
 
@@ -546,6 +546,9 @@ def run_profile_case(case):
         A = torch.rand((192, 256, 256), device="cuda")
         B = torch.rand((192, 256, 256), device="cuda")
         capi.wp_facewise(A, B, prec="bf16x3")
+    elif case == "wprod":
+        A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
+        capi.wp_wprod(A, B, WORKLOAD["L"], prec="bf16x3")
     elif case == "jacobi":
         A = torch.from_numpy(synth.hsi_cube(256, 256, 16, seed=0, dtype=np.float32)).cuda()
         capi.wp_wsvd(A, 3, 20)

@@ -8,6 +8,12 @@
 //           hi = bf16(x), lo = bf16(x - hi), so hi + lo carries ~16 bits of
 //           the mantissa; the kernel accumulates hi*hi + hi*lo + lo*hi (the
 //           dropped lo*lo term is ~2^-18 relative) into one FP32 accumulator.
+//   FP8     E4M3 operands with one scale per wavelet-domain slice and operand:
+//           s = amax(|X_k|) / 448 (448 = largest finite E4M3), q = e4m3(x / s);
+//           kind::f8f6f4 MMAs accumulate q_a q_b in FP32 and the epilogue
+//           multiplies by s_a[k] s_b[k].  The scales are taken on the
+//           wavelet-domain slices, after the lifting has mixed the 2^L
+//           spatial slices of a group.
 //
 // Pipeline (one CTA per 128 x BN output tile of one slice, 6 warps):
 //   warp 0      TMA producer: loads the K-major BF16 tiles of A (128 x 64)
@@ -21,10 +27,12 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "lift_math.cuh"
 #include "tc_ptx.cuh"
 
 namespace wp {
@@ -83,6 +91,66 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
   }
 }
 
+// ---- FP8 operand preparation ------------------------------------------------------------
+
+// amax_bits[b] = max |X[b]| (as the bit pattern of a non-negative float, so
+// integer atomicMax orders it); one CTA row of the grid per slice.
+__global__ void __launch_bounds__(256) amax_slices_kernel(const float* __restrict__ X, int64_t per_slice,
+                                                          unsigned* __restrict__ amax_bits) {
+  const int64_t b = blockIdx.y;
+  const float* x = X + b * per_slice;
+  float m = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < per_slice; i += int64_t(gridDim.x) * blockDim.x)
+    m = fmaxf(m, fabsf(__ldg(x + i)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax_bits + b, __float_as_uint(m));
+}
+
+__device__ __forceinline__ float fp8_scale(unsigned amax_bits) {
+  const float a = __uint_as_float(amax_bits);
+  return a > 0.f ? a / 448.f : 1.f;
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float x) {
+  return static_cast<uint8_t>(__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3));
+}
+
+// in (batch, R, C) fp32 -> q (batch, R, Cp) e4m3 with the slice's scale.
+__global__ void __launch_bounds__(256) quant_rows_kernel(const float* __restrict__ in, uint8_t* __restrict__ q,
+                                                         const unsigned* __restrict__ amax_bits, int64_t rows_per_slice,
+                                                         int64_t total_rows, int C, int Cp) {
+  const int64_t total = total_rows * Cp;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / Cp;
+    const int c = int(i - r * Cp);
+    const float inv = 1.f / fp8_scale(amax_bits[r / rows_per_slice]);
+    q[i] = (c < C) ? to_e4m3(__ldg(in + r * C + c) * inv) : uint8_t(0);
+  }
+}
+
+// in (batch, R, C) fp32 -> q (batch, C, Rp) e4m3 (transposed) with the slice's scale.
+__global__ void __launch_bounds__(256) quant_transpose_kernel(const float* __restrict__ in, uint8_t* __restrict__ q,
+                                                              const unsigned* __restrict__ amax_bits, int R, int C,
+                                                              int Rp, int batch) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int b = blockIdx.z; b < batch; b += gridDim.z) {
+    const float* src = in + int64_t(b) * R * C;
+    const float inv = 1.f / fp8_scale(amax_bits[b]);
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int r = r0 + i, c = c0 + threadIdx.x;
+      tile[i][threadIdx.x] = (r < R && c < C) ? __ldg(src + int64_t(r) * C + c) : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+      const int c = c0 + i, r = r0 + threadIdx.x;
+      if (c < C && r < Rp) q[(int64_t(b) * C + c) * Rp + r] = to_e4m3(tile[threadIdx.x][i] * inv);
+    }
+    __syncthreads();
+  }
+}
+
 // ---- the GEMM kernel ---------------------------------------------------------------
 
 namespace tc {
@@ -93,21 +161,25 @@ constexpr int THREADS = 192;
 
 template <int BN, int NPROD, int STAGES>
 struct Layout {
-  static constexpr int NCOPY = (NPROD == 1) ? 1 : 2;
-  static constexpr int A_TILE = BM * BK * 2;
-  static constexpr int B_TILE = BN * BK * 2;
+  static constexpr int NCOPY = (NPROD == 3) ? 2 : 1;   // BF16x3 keeps hi and lo copies
+  static constexpr int A_TILE = BM * 128;               // 128-byte K rows (64 BF16 or 128 FP8)
+  static constexpr int B_TILE = BN * 128;
   static constexpr int STAGE = NCOPY * (A_TILE + B_TILE);
   static constexpr int BAR_OFF = STAGES * STAGE;
   static constexpr int SMEM = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;   // + alignment slack
   static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
 };
 
+// NPROD: 1 = BF16, 3 = BF16x3, 8 = FP8 E4M3 (then sa_bits / sb_bits hold the
+// per-slice amax of each operand and the epilogue applies s_a s_b).
 template <int BN, int NPROD, int STAGES>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                   float* __restrict__ C, int M, int N, int K, int* status) {
+                   float* __restrict__ C, int M, int N, int K, int* status, const unsigned* __restrict__ sa_bits,
+                   const unsigned* __restrict__ sb_bits) {
   using Lay = Layout<BN, NPROD, STAGES>;
+  constexpr int BKE = (NPROD == 8) ? 128 : BK;          // K elements per 128-byte row
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFF);
@@ -117,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
-  const int nk = (K + BK - 1) / BK;
+  const int nk = (K + BKE - 1) / BKE;
 
   auto a_tile = [&](int s, int copy) { return smem + s * Lay::STAGE + copy * Lay::A_TILE; };
   auto b_tile = [&](int s, int copy) {
@@ -149,10 +221,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (kb >= STAGES) ok = ptx::mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, status);
       if (!ok) break;
       ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
-      ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BK, m0, b, &full[s]);
-      if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BK, m0, b, &full[s]);
-      ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BK, n0, b, &full[s]);
-      if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BK, n0, b, &full[s]);
+      ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BKE, m0, b, &full[s]);
+      if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BKE, m0, b, &full[s]);
+      ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BKE, n0, b, &full[s]);
+      if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BKE, n0, b, &full[s]);
       ++issued;
     }
     if (!ok) {
@@ -162,16 +234,20 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
+    constexpr uint32_t idesc = (NPROD == 8) ? ptx::idesc_e4m3_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
     for (int kb = 0; kb < nk && ok; ++kb) {
       const int s = kb % STAGES;
       ok = ptx::mbar_wait(&full[s], (kb / STAGES) & 1, status);
       if (!ok) break;
       ptx::tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {            // 4 MMAs of 32 bytes of K per 128-byte row
         const uint64_t ah = ptx::sdesc_kmajor_sw128(a_tile(s, 0) + kk * 32);
         const uint64_t bh = ptx::sdesc_kmajor_sw128(b_tile(s, 0) + kk * 32);
+        if (NPROD == 8) {
+          ptx::mma_e4m3(tmem, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          continue;
+        }
         ptx::mma_bf16(tmem, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
         if (NPROD == 3) {
           const uint64_t al = ptx::sdesc_kmajor_sw128(a_tile(s, 1) + kk * 32);
@@ -192,11 +268,17 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int row = m0 + quad * 32 + lane;
       float* crow = C + (int64_t(b) * M + row) * N;
       const bool vec = (N % 4) == 0;
+      float scale = 1.f;
+      if constexpr (NPROD == 8) scale = fp8_scale(sa_bits[b]) * fp8_scale(sb_bits[b]);
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= N) break;
         float v[32];
         ptx::tmem_ld_32cols(tmem + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
+        if constexpr (NPROD == 8) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] *= scale;
+        }
         if (row < M) {
           const int col = n0 + c0;
           if (vec && col + 32 <= N) {
@@ -222,6 +304,295 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace tc
 
+// ---- fused w-product: lift + split producers, inverse-lift epilogue ------------------------
+//
+// For C = A *w B (no transposes, 1 <= L <= 5) the operand preparation and
+// the inverse transform are folded into the neighbouring passes:
+//   lift_split_rows_kernel       spatial A (p, n1, n2) -> W(A) as BF16 hi/lo,
+//                                K-major (p, n1, Kp), Mallat order: one HBM pass
+//   lift_split_transpose_kernel  spatial B (p, n2, n4) -> W(B)^T as BF16 hi/lo,
+//                                K-major (p, n4, Kp), transposed through a
+//                                shared-memory tile: one HBM pass
+//   tc_gemm_ilift_kernel         one CTA owns a 128 x BN tile of all G = 2^L
+//                                wavelet-domain slices of a tube group, with G
+//                                TMEM accumulators of BN = 512 / G columns; the
+//                                epilogue reads the G accumulators of a few
+//                                columns at a time, applies W^{-1} across them in
+//                                registers (Eq. 3) and stores spatial C.  The
+//                                wavelet-domain product never reaches HBM.
+
+template <int L, int VEC>
+__global__ void __launch_bounds__(256) lift_split_rows_kernel(const float* __restrict__ in,
+                                                              __nv_bfloat16* __restrict__ hi,
+                                                              __nv_bfloat16* __restrict__ lo, int64_t p, int R,
+                                                              int C, int Cp, int64_t total) {
+  constexpr int G = 1 << L;
+  const int64_t plane = int64_t(R) * C;
+  const int64_t nvec = plane / VEC;
+  for (int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; item < total;
+       item += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = item / nvec;
+    const int64_t e = (item - g * nvec) * VEC;
+    const int r = int(e / C), c = int(e - int64_t(r) * C);
+    float v[G][VEC];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const float* src = in + (g * G + t) * plane + e;
+      if constexpr (VEC == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+        v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
+      } else {
+        v[t][0] = __ldg(src);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      float x[G], y[G];
+#pragma unroll
+      for (int t = 0; t < G; ++t) x[t] = v[t][j];
+      lift_group<L>(x, y);
+#pragma unroll
+      for (int t = 0; t < G; ++t) v[t][j] = y[t];
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int64_t o = mallat_slice<L>(t, g, p) * int64_t(R) * Cp + int64_t(r) * Cp + c;
+      if constexpr (VEC == 4) {
+        __nv_bfloat16 h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) split_bf16(v[t][j], h[j], l[j]);
+        *reinterpret_cast<uint2*>(hi + o) = *reinterpret_cast<uint2*>(h);
+        if (lo) *reinterpret_cast<uint2*>(lo + o) = *reinterpret_cast<uint2*>(l);
+      } else {
+        __nv_bfloat16 h, l;
+        split_bf16(v[t][0], h, l);
+        hi[o] = h;
+        if (lo) lo[o] = l;
+      }
+    }
+  }
+}
+
+// Spatial B (p, R, C) -> Mallat-ordered transposed BF16 hi/lo (p, C, Rp).
+// A CTA (256 threads) takes a TR x CW tile of the plane (TR = min(64, 512/G)
+// input rows, CW = 2048/TR columns) of one tube group: coalesced loads into
+// shared memory, the lift across the group's G slices in registers, then
+// every thread writes 8 consecutive K-elements of one output row as a
+// 16-byte vector per BF16 copy.
+template <int L>
+__global__ void __launch_bounds__(256) lift_split_transpose_kernel(const float* __restrict__ in,
+                                                                   __nv_bfloat16* __restrict__ hi,
+                                                                   __nv_bfloat16* __restrict__ lo, int64_t p, int R,
+                                                                   int C, int Rp) {
+  constexpr int G = 1 << L;
+  constexpr int E = (G <= 16) ? 2048 : 1024;          // tile elements per slice (smem <= 132 KB)
+  constexpr int PER = E / 256;
+  constexpr int TR = (512 / G) < 64 ? (512 / G) : 64;
+  constexpr int CW = E / TR;
+  constexpr int LD = CW + 1;
+  extern __shared__ float tile[];   // [G][TR][LD]
+  const int c0 = blockIdx.x * CW, r0 = blockIdx.y * TR;
+  const int64_t g = blockIdx.z;
+  const int64_t plane = int64_t(R) * C;
+  const int tid = threadIdx.x;
+#pragma unroll 2
+  for (int t = 0; t < G; ++t) {
+    const float* src = in + (g * G + t) * plane;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = tid + 256 * q, i = idx / CW, j = idx % CW;
+      const int r = r0 + i, c = c0 + j;
+      tile[(t * TR + i) * LD + j] = (r < R && c < C) ? __ldg(src + int64_t(r) * C + c) : 0.f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = tid + 256 * q, i = idx / CW, j = idx % CW;
+    float x[G], y[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) x[t] = tile[(t * TR + i) * LD + j];
+    lift_group<L>(x, y);
+#pragma unroll
+    for (int t = 0; t < G; ++t) tile[(t * TR + i) * LD + j] = y[t];
+  }
+  __syncthreads();
+  const int cl = tid / (TR / 8), chunk = tid % (TR / 8);
+  const int c = c0 + cl, rs = r0 + chunk * 8;
+  if (tid < CW * (TR / 8) && c < C && rs < Rp) {
+#pragma unroll 2
+    for (int t = 0; t < G; ++t) {
+      const int64_t s = mallat_slice<L>(t, g, p);
+      __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) split_bf16(tile[(t * TR + chunk * 8 + q) * LD + cl], h[q], l[q]);
+      const int64_t o = (s * C + c) * Rp + rs;
+      *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+      if (lo) *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+    }
+  }
+}
+
+namespace tc {
+
+template <int L, int NPROD, int STAGES, int TMEM = 512>
+struct FusedLayout {
+  static constexpr int G = 1 << L;
+  static constexpr int TMEM_COLS = TMEM;
+  static constexpr int BN = TMEM / G;                   // G accumulators fill the CTA's TMEM columns
+  static constexpr int NCOPY = (NPROD == 1) ? 1 : 2;
+  static constexpr int A_TILE = BM * BK * 2;
+  static constexpr int B_TILE = BN * BK * 2;
+  static constexpr int STAGE = NCOPY * (A_TILE + B_TILE);
+  static constexpr int BAR_OFF = STAGES * STAGE;
+  static constexpr int SMEM = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;
+  static constexpr int CH = 64 / G < 16 ? 64 / G : 16;  // columns per epilogue chunk (registers: G * CH = 64)
+};
+
+template <int L, int NPROD, int STAGES, int TMEM>
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_ilift_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                         const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                         float* __restrict__ C, int M, int N, int K, int64_t p, int* status) {
+  using Lay = FusedLayout<L, NPROD, STAGES, TMEM>;
+  constexpr int G = Lay::G, BN = Lay::BN, CH = Lay::CH;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFF);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int64_t g = blockIdx.z;
+  const int nk = (K + BK - 1) / BK;
+  const int iters = G * nk;
+
+  auto a_tile = [&](int s, int copy) { return smem + s * Lay::STAGE + copy * Lay::A_TILE; };
+  auto b_tile = [&](int s, int copy) {
+    return smem + s * Lay::STAGE + Lay::NCOPY * Lay::A_TILE + copy * Lay::B_TILE;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(accum, 1);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) ptx::tmem_alloc(tmem_slot, TMEM);
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    ptx::tma_prefetch_desc(&tmAh);
+    ptx::tma_prefetch_desc(&tmBh);
+    int issued = 0;
+    for (int it = 0; it < iters && ok; ++it) {
+      const int s = it % STAGES;
+      const int t = it / nk, kb = it % nk;
+      const int z = int(mallat_slice<L>(t, g, p));
+      if (it >= STAGES) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
+      if (!ok) break;
+      ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
+      ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BK, m0, z, &full[s]);
+      if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BK, m0, z, &full[s]);
+      ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BK, n0, z, &full[s]);
+      if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BK, n0, z, &full[s]);
+      ++issued;
+    }
+    if (!ok) {
+      for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
+        ptx::mbar_wait(&full[it % STAGES], (it / STAGES) & 1, nullptr, 100000000ull);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
+    for (int it = 0; it < iters && ok; ++it) {
+      const int s = it % STAGES;
+      const int t = it / nk, kb = it % nk;
+      ok = ptx::mbar_wait(&full[s], (it / STAGES) & 1, status);
+      if (!ok) break;
+      ptx::tc_fence_after();
+      const uint32_t d = tmem + uint32_t(t * BN);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t ah = ptx::sdesc_kmajor_sw128(a_tile(s, 0) + kk * 32);
+        const uint64_t bh = ptx::sdesc_kmajor_sw128(b_tile(s, 0) + kk * 32);
+        ptx::mma_bf16(d, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        if (NPROD == 3) {
+          const uint64_t al = ptx::sdesc_kmajor_sw128(a_tile(s, 1) + kk * 32);
+          const uint64_t bl = ptx::sdesc_kmajor_sw128(b_tile(s, 1) + kk * 32);
+          ptx::mma_bf16(d, ah, bl, idesc, 1u);
+          ptx::mma_bf16(d, al, bh, idesc, 1u);
+        }
+      }
+      ptx::mma_commit(&empty[s]);
+    }
+    ptx::mma_commit(accum);
+  } else if (warp >= 2) {
+    ok = ptx::mbar_wait(accum, 0, status);
+    ptx::tc_fence_after();
+    if (ok) {
+      const int quad = warp & 3;
+      const int row = m0 + quad * 32 + lane;
+      const uint32_t lane_base = tmem + (uint32_t(quad * 32) << 16);
+      const bool vec = (N % 4) == 0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += CH) {
+        if (n0 + c0 >= N) break;
+        float v[G][CH];
+#pragma unroll
+        for (int t = 0; t < G; ++t) ptx::tmem_ld_cols<CH>(lane_base + uint32_t(t * BN + c0), v[t]);
+        if (row < M) {
+          // inverse transform across the group's G slices, column by column
+#pragma unroll
+          for (int j = 0; j < CH; ++j) {
+            float y[G], x[G];
+#pragma unroll
+            for (int t = 0; t < G; ++t) y[t] = v[t][j];
+            ilift_group<L>(y, x);
+#pragma unroll
+            for (int t = 0; t < G; ++t) v[t][j] = x[t];
+          }
+          const int col = n0 + c0;
+#pragma unroll
+          for (int t = 0; t < G; ++t) {
+            float* dst = C + ((g * G + t) * M + row) * int64_t(N) + col;
+            if (vec && col + CH <= N) {
+#pragma unroll
+              for (int j = 0; j < CH; j += 4 < CH ? 4 : CH) {
+                if constexpr (CH >= 4)
+                  *reinterpret_cast<float4*>(dst + j) = make_float4(v[t][j], v[t][j + 1], v[t][j + 2], v[t][j + 3]);
+                else
+                  *reinterpret_cast<float2*>(dst + j) = make_float2(v[t][j], v[t][j + 1]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < CH; ++j)
+                if (col + j < N) dst[j] = v[t][j];
+            }
+          }
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    ptx::tc_fence_after();
+    if (!ok) ptx::mbar_wait(accum, 0, nullptr, 100000000ull);
+    __syncwarp();
+    ptx::tmem_dealloc(tmem, TMEM);
+  }
+}
+
+}  // namespace tc
+
 // ---- host side -------------------------------------------------------------------------
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -237,24 +608,35 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Tensor map of a (batch, rows, Kp) BF16 array, box = (64, box_rows, 1), 128B swizzle.
+// Tensor map of a (batch, rows, Kp) operand array whose rows are K-major with
+// `esize`-byte elements (2: BF16, 1: FP8 bytes); box = one 128-byte row
+// segment x box_rows rows, 128B swizzle.
 static int make_map(CUtensorMap* map, const void* base, int64_t K, int64_t Kp, int64_t rows, int64_t batch,
-                    int box_rows) {
+                    int box_rows, int esize = 2) {
   auto fn = encode_fn();
   if (!fn) return WP_ERR_CUDA;
   cuuint64_t dims[3] = {cuuint64_t(K), cuuint64_t(rows), cuuint64_t(batch)};
-  cuuint64_t strides[2] = {cuuint64_t(Kp * 2), cuuint64_t(rows * Kp * 2)};
-  cuuint32_t box[3] = {cuuint32_t(tc::BK), cuuint32_t(box_rows), 1};
+  cuuint64_t strides[2] = {cuuint64_t(Kp * esize), cuuint64_t(rows * Kp * esize)};
+  cuuint32_t box[3] = {cuuint32_t(128 / esize), cuuint32_t(box_rows), 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+  const CUtensorMapDataType dt = (esize == 2) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? WP_OK : WP_ERR_CUDA;
 }
 
 static int64_t pad8(int64_t k) { return (k + 7) / 8 * 8; }
+static int64_t pad16(int64_t k) { return (k + 15) / 16 * 16; }
 
 size_t tc_facewise_workspace(int64_t M, int64_t N, int64_t K, int64_t p, int prec) {
+  if (prec == WP_PREC_FP8) {
+    Sizer s;
+    s.take<uint8_t>(size_t(p) * M * pad16(K));
+    s.take<uint8_t>(size_t(p) * N * pad16(K));
+    s.take<unsigned>(2 * size_t(p));
+    return s.bytes();
+  }
   if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3) return 0;
   const int64_t Kp = pad8(K);
   const int ncopy = (prec == WP_PREC_BF16X3) ? 2 : 1;
@@ -286,7 +668,8 @@ static int split_operand(const float* X, int64_t rows, int64_t K, int64_t Kp, in
 
 template <int BN, int NPROD, int STAGES>
 static int launch_gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
-                       float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st, const char* name) {
+                       float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st, const char* name,
+                       const unsigned* sa = nullptr, const unsigned* sb = nullptr) {
   using Lay = tc::Layout<BN, NPROD, STAGES>;
   static bool attr = false;
   if (!attr) {
@@ -297,12 +680,62 @@ static int launch_gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUten
   const dim3 grid{unsigned((N + BN - 1) / BN), unsigned((M + tc::BM - 1) / tc::BM), unsigned(p)};
   WP_PROFILE(name, st);
   tc::tc_gemm_kernel<BN, NPROD, STAGES><<<grid, tc::THREADS, Lay::SMEM, st>>>(ah, al, bh, bl, C, int(M), int(N),
-                                                                              int(K), device_status_ptr());
+                                                                              int(K), device_status_ptr(), sa, sb);
   return launch_status();
+}
+
+// FP8: per-slice amax of both operands, E4M3 quantisation (K-major, rows
+// padded to 16 bytes), E4M3 GEMM with the scales applied in the epilogue.
+static int tc_facewise_fp8(const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K, int64_t p,
+                           bool transA, bool transB, void* ws, size_t ws_bytes, cudaStream_t st) {
+  const int64_t Kp = pad16(K);
+  Carver cv(ws, ws_bytes);
+  uint8_t* A8 = cv.take<uint8_t>(size_t(p) * M * Kp);
+  uint8_t* B8 = cv.take<uint8_t>(size_t(p) * N * Kp);
+  unsigned* amax = cv.take<unsigned>(2 * size_t(p));
+  if (!cv.ok) return WP_ERR_WORKSPACE;
+  WP_CUDA_TRY(cudaMemsetAsync(amax, 0, 2 * size_t(p) * sizeof(unsigned), st));
+  {
+    const dim3 grid{unsigned(std::max<int64_t>(1, std::min<int64_t>(64, (M * K + 255) / 256))), unsigned(p), 1u};
+    WP_PROFILE("amax_fp8", st);
+    amax_slices_kernel<<<grid, 256, 0, st>>>(A, M * K, amax);
+    WP_TRY(launch_status());
+  }
+  {
+    const dim3 grid{unsigned(std::max<int64_t>(1, std::min<int64_t>(64, (N * K + 255) / 256))), unsigned(p), 1u};
+    WP_PROFILE("amax_fp8", st);
+    amax_slices_kernel<<<grid, 256, 0, st>>>(B, N * K, amax + p);
+    WP_TRY(launch_status());
+  }
+  auto quant = [&](const float* X, int64_t rows, bool kmajor_in, uint8_t* out, const unsigned* am) -> int {
+    if (kmajor_in) {
+      const int64_t total = p * rows * Kp;
+      const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
+      WP_PROFILE("quant_fp8", st);
+      quant_rows_kernel<<<unsigned(blocks), 256, 0, st>>>(X, out, am, rows, p * rows, int(K), int(Kp));
+      return launch_status();
+    }
+    const dim3 grid{unsigned((rows + 31) / 32), unsigned((Kp + 31) / 32), unsigned(std::min<int64_t>(p, 65535))};
+    WP_PROFILE("quant_transpose_fp8", st);
+    quant_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(X, out, am, int(K), int(rows), int(Kp), int(p));
+    return launch_status();
+  };
+  WP_TRY(quant(A, M, !transA, A8, amax));
+  WP_TRY(quant(B, N, transB, B8, amax + p));
+  CUtensorMap ma, mb;
+  constexpr int BN = 256;
+  WP_TRY(make_map(&ma, A8, K, Kp, M, p, tc::BM, 1));
+  WP_TRY(make_map(&mb, B8, K, Kp, N, p, BN, 1));
+  return launch_gemm<BN, 8, 4>(ma, ma, mb, mb, C, M, N, K, p, st, "tc_gemm_fp8", amax, amax + p);
 }
 
 int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K, int64_t p, bool transA,
                 bool transB, int prec, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (p > 65535 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return WP_ERR_SHAPE;
+  if (prec == WP_PREC_FP8) {
+    if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
+    return tc_facewise_fp8(A, B, C, M, N, K, p, transA, transB, ws, ws_bytes, st);
+  }
   if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3) return WP_ERR_UNSUPPORTED;
   if (p > 65535 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return WP_ERR_SHAPE;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
@@ -331,6 +764,113 @@ int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, 
   WP_TRY(make_map(&mah, Ah, K, Kp, M, p, tc::BM));
   WP_TRY(make_map(&mbh, Bh, K, Kp, N, p, BN));
   return launch_gemm<BN, 1, 4>(mah, mah, mbh, mbh, C, M, N, K, p, st, "tc_gemm_bf16");
+}
+
+}  // namespace wp
+
+namespace wp {
+
+template <int L>
+static int launch_lift_split_transpose(const float* B, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t p, int R, int C,
+                                       int Rp, cudaStream_t st) {
+  constexpr int G = 1 << L;
+  constexpr int E = (G <= 16) ? 2048 : 1024;
+  constexpr int TR = (512 / G) < 64 ? (512 / G) : 64;
+  constexpr int CW = E / TR;
+  const size_t smem = size_t(G) * TR * (CW + 1) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    WP_CUDA_TRY(cudaFuncSetAttribute(lift_split_transpose_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem)));
+    attr = true;
+  }
+  const dim3 grid{unsigned((C + CW - 1) / CW), unsigned((Rp + TR - 1) / TR), unsigned(p >> L)};
+  WP_PROFILE("lift_split_transpose_bf16", st);
+  lift_split_transpose_kernel<L><<<grid, 256, smem, st>>>(B, hi, lo, p, R, C, Rp);
+  return launch_status();
+}
+
+template <int L>
+static int launch_lift_split_rows(const float* A, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t p, int R, int C,
+                                  int Cp, cudaStream_t st) {
+  const bool v4 = (C % 4 == 0) && aligned16(A);
+  const int64_t plane = int64_t(R) * C;
+  const int64_t total = (p >> L) * (v4 ? plane / 4 : plane);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
+  WP_PROFILE("lift_split_bf16", st);
+  if (v4) lift_split_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(A, hi, lo, p, R, C, Cp, total);
+  else lift_split_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(A, hi, lo, p, R, C, Cp, total);
+  return launch_status();
+}
+
+// TMEM = 256 halves the tile width so that two CTAs (each with its own
+// 256 TMEM columns and < 113 KB of shared memory) share an SM; TMEM = 512
+// keeps one CTA per SM with the widest tile.
+template <int L, int NPROD, int TMEM>
+static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
+                        float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st) {
+  using Probe = tc::FusedLayout<L, NPROD, 1, TMEM>;
+  constexpr int BUDGET = (TMEM == 512) ? 196608 : 110592;
+  constexpr int STAGES = std::min(6, BUDGET / Probe::STAGE);
+  using Lay = tc::FusedLayout<L, NPROD, STAGES, TMEM>;
+  static bool attr = false;
+  if (!attr) {
+    WP_CUDA_TRY(cudaFuncSetAttribute(tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
+    attr = true;
+  }
+  const dim3 grid{unsigned((N + Lay::BN - 1) / Lay::BN), unsigned((M + tc::BM - 1) / tc::BM), unsigned(p >> L)};
+  WP_PROFILE(NPROD == 3 ? "tc_gemm_ilift_bf16x3" : "tc_gemm_ilift_bf16", st);
+  tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM><<<grid, tc::THREADS, Lay::SMEM, st>>>(
+      ah, al, bh, bl, C, int(M), int(N), int(K), p, device_status_ptr());
+  return launch_status();
+}
+
+template <int L>
+static int fused_levels(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
+                        bool x3, __nv_bfloat16* Ah, __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl,
+                        int64_t Kp, cudaStream_t st) {
+  WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
+  WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
+  CUtensorMap mah, mal, mbh, mbl;
+  // one CTA per SM with all 512 TMEM columns: measured faster at L = 3 than
+  // two CTAs with 256 columns each (narrower N = 32 tiles, 2-stage rings)
+  constexpr int TMEM = 512;
+  constexpr int BN = tc::FusedLayout<L, 1, 1, TMEM>::BN;
+  WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
+  WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, BN));
+  if (x3) {
+    WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, tc::BM));
+    WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, BN));
+    return launch_fused<L, 3, TMEM>(mah, mal, mbh, mbl, C, n1, n4, n2, p, st);
+  }
+  return launch_fused<L, 1, TMEM>(mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
+}
+
+// C = A *w B for tensor-core precisions with the transform fused into the
+// operand preparation and the GEMM epilogue.  WP_ERR_UNSUPPORTED when the
+// arguments fall outside the fused path (the caller then uses the unfused one).
+int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p, int L,
+                   int prec, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3) return WP_ERR_UNSUPPORTED;
+  if (L < 1 || L > 5) return WP_ERR_UNSUPPORTED;
+  if ((p >> L) > 65535 || n1 > INT32_MAX || n2 > INT32_MAX || n4 > INT32_MAX) return WP_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
+  const int64_t Kp = pad8(n2);
+  const bool x3 = (prec == WP_PREC_BF16X3);
+  Carver cv(ws, ws_bytes);
+  __nv_bfloat16* Ah = cv.take<__nv_bfloat16>(size_t(p) * n1 * Kp);
+  __nv_bfloat16* Bh = cv.take<__nv_bfloat16>(size_t(p) * n4 * Kp);
+  __nv_bfloat16* Al = x3 ? cv.take<__nv_bfloat16>(size_t(p) * n1 * Kp) : nullptr;
+  __nv_bfloat16* Bl = x3 ? cv.take<__nv_bfloat16>(size_t(p) * n4 * Kp) : nullptr;
+  if (!cv.ok) return WP_ERR_WORKSPACE;
+  switch (L) {
+    case 1: return fused_levels<1>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
+    case 2: return fused_levels<2>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
+    case 3: return fused_levels<3>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
+    case 4: return fused_levels<4>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
+    default: return fused_levels<5>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
+  }
 }
 
 }  // namespace wp

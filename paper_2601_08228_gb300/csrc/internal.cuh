@@ -21,6 +21,10 @@ size_t tc_facewise_workspace(int64_t M, int64_t N, int64_t K, int64_t p, int pre
 int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K,
                 int64_t p, bool transA, bool transB, int prec, void* ws, size_t ws_bytes,
                 cudaStream_t st);
+// Fused tensor-core w-product (lift + split producers, inverse-lift epilogue);
+// WP_ERR_UNSUPPORTED outside its domain (no transposes, 1 <= L <= 5).
+int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
+                   int64_t p, int L, int prec, void* ws, size_t ws_bytes, cudaStream_t st);
 
 }  // namespace wp
 

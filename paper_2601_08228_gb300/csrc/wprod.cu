@@ -3,7 +3,9 @@
 //   C = W^{-1}( W(op A) Delta W(op B) )
 //
 // Forward: lift A and B (one fused pass each), face-product of the p
-// wavelet-domain slices, inverse-lift C.  The transform acts tube by tube,
+// wavelet-domain slices, inverse-lift C.  For the tensor-core precisions
+// without transposes the transform is folded into the operand preparation
+// and the GEMM epilogue instead (tc_wprod_fused in gemm_tc.cu).  The transform acts tube by tube,
 // so a transposed operand is lifted in its stored layout and the transpose is
 // applied by the GEMM (Thm 2.1: W(A^T) = W(A)^T).
 //
@@ -94,6 +96,10 @@ extern "C" int wp_wprod(const float* A, const float* B, float* C, int64_t n1, in
   Sizer need;
   wprod_layout(n1, n2, n4, p, prec, need);
   if (ws == nullptr || ws_bytes < need.bytes()) return WP_ERR_WORKSPACE;
+  if (!transA && !transB && prec != WP_PREC_FP32) {
+    const int st_fused = tc_wprod_fused(A, B, C, n1, n2, n4, p, L, prec, ws, ws_bytes, as_stream(stream));
+    if (st_fused != WP_ERR_UNSUPPORTED) return st_fused;
+  }
   Carver cv(ws, ws_bytes);
   float* Ah = cv.take<float>(size_t(p) * n1 * n2);
   float* Bh = cv.take<float>(size_t(p) * n2 * n4);

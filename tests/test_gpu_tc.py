@@ -115,3 +115,59 @@ def test_backward_bf16x3_parity():
     assert O.rel_fro(host(dA), rA) <= TOL_X3
     assert O.rel_fro(host(dB), rB) <= TOL_X3
     assert capi.wp_get_device_error() == 0
+
+
+FUSED_CASES = [
+    # p, n1, n2, n4, L  (no transposes, 1 <= L <= 5: the fused lift/GEMM/inverse-lift path)
+    (6, 130, 70, 77, 1),        # 3 groups, ragged M and N, N not a multiple of 4
+    (8, 64, 40, 300, 2),        # N over several 128-wide tiles
+    (24, 200, 33, 64, 3),       # K not a multiple of 8, 3 groups
+    (32, 17, 64, 40, 4),        # one short M tile, BN = 32
+    (64, 50, 96, 21, 5),        # BN = 16, two groups
+    (16, 1, 1, 1, 4),           # degenerate
+]
+
+
+@pytest.mark.parametrize("p,n1,n2,n4,L", FUSED_CASES)
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_wprod_fused_path(p, n1, n2, n4, L, prec):
+    A, B = rand((p, n1, n2), 11), rand((p, n2, n4), 12)
+    C = host(capi.wp_wprod(dev(A), dev(B), L, prec=prec))
+    err = O.rel_fro(C, O.wprod(A, B, L))
+    assert err <= (TOL_X3 if prec == "bf16x3" else TOL_BF16), err
+    assert capi.wp_get_device_error() == 0
+
+
+@pytest.mark.parametrize("p,M,N,K", [(4, 128, 256, 128), (3, 200, 300, 100), (2, 5, 7, 9), (1, 1000, 520, 1030)])
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, True)])
+def test_facewise_fp8(p, M, N, K, tA, tB):
+    """E4M3 with one scale per slice and operand: reported precision (3
+    mantissa bits; ~3% relative error on random data), checked loosely."""
+    A = rand((p, K, M) if tA else (p, M, K), 13)
+    B = rand((p, N, K) if tB else (p, K, N), 14)
+    C = host(capi.wp_facewise(dev(A), dev(B), transA=tA, transB=tB, prec="fp8"))
+    At = np.swapaxes(A, 1, 2) if tA else A
+    Bt = np.swapaxes(B, 1, 2) if tB else B
+    assert O.rel_fro(C, O.facewise(At, Bt)) <= 0.08
+
+
+def test_fp8_per_slice_scales():
+    """Slices scaled by 10^U[-3, 3] keep their own relative accuracy: every
+    slice's error stays at the E4M3 level (a single global scale would flush
+    the small slices to zero)."""
+    A, B = synth.scaled_pair(64, 64, 48, 16, seed=0)
+    C = host(capi.wp_facewise(dev(A), dev(B), prec="fp8"))
+    ref = O.facewise(A, B)
+    for k in range(16):
+        assert O.rel_fro(C[k], ref[k]) <= 0.08
+
+
+def test_wprod_fp8_and_backward():
+    p, n1, n2, n4, L = 16, 64, 80, 48, 4
+    A, B, G = rand((p, n1, n2), 15), rand((p, n2, n4), 16), rand((p, n1, n4), 17)
+    C = host(capi.wp_wprod(dev(A), dev(B), L, prec="fp8"))
+    assert O.rel_fro(C, O.wprod(A, B, L)) <= 0.08
+    dA, dB = capi.wp_wprod_backward(dev(A), dev(B), dev(G), L, prec="fp8")
+    rA, rB = O.wprod_grad(A, B, G, L)
+    assert O.rel_fro(host(dA), rA) <= 0.08 and O.rel_fro(host(dB), rB) <= 0.08
+    assert capi.wp_get_device_error() == 0
