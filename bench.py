@@ -530,6 +530,29 @@ def _extras(capi, args):
     step = a.elapsed_time(b) / 10
     out["deblur_512x512x128"] = {"ms_per_step": step, "ms_200_steps": 200 * step,
                                  "tflops": 2 * 2 * n ** 3 * p / (step / 1e3) / 1e12, "prec": "bf16x3"}
+    del Kd, Yd, X, ws
+    # precision study: A 1024x1024x256 by B 1024x512x256, per-slice 10^U[-3,3] scales, L = 4
+    A, B = synth.scaled_pair(1024, 1024, 512, 256, seed=0)
+    ref = O.wprod(A, B, 4)
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    flops = 2.0 * 1024 * 1024 * 512 * 256
+    study = {}
+    for prec in ("fp32", "bf16x3", "bf16", "fp8"):
+        Cd = torch.empty((256, 1024, 512), device="cuda")
+        wsb = torch.empty(capi.wp_wprod_workspace(1024, 1024, 512, 256, 4, prec), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            capi.wp_wprod(Ad, Bd, 4, prec=prec, out=Cd, ws=wsb)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(3):
+            capi.wp_wprod(Ad, Bd, 4, prec=prec, out=Cd, ws=wsb)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 3 / 1e3
+        study[prec] = {"tflops": flops / t / 1e12, "ms": t * 1e3,
+                       "rel_err": O.rel_fro(Cd.cpu().numpy(), ref)}
+        del Cd, wsb
+    out["precision_1024x1024x256_by_1024x512x256_L4"] = study
     return out
 
 

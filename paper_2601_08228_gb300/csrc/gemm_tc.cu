@@ -829,10 +829,24 @@ static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUte
 template <int L>
 static int fused_levels(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
                         bool x3, __nv_bfloat16* Ah, __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl,
-                        int64_t Kp, cudaStream_t st) {
+                        int64_t Kp, float* Chat, cudaStream_t st) {
   WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
   WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
   CUtensorMap mah, mal, mbh, mbl;
+  if (Chat) {
+    // wide-tile GEMM into the wavelet-domain C_hat, then the inverse transform
+    WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
+    if (x3) {
+      WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, tc::BM));
+      WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, 128));
+      WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, 128));
+      WP_TRY((launch_gemm<128, 3, 3>(mah, mal, mbh, mbl, Chat, n1, n4, n2, p, st, "tc_gemm_bf16x3")));
+    } else {
+      WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, 256));
+      WP_TRY((launch_gemm<256, 1, 4>(mah, mah, mbh, mbh, Chat, n1, n4, n2, p, st, "tc_gemm_bf16")));
+    }
+    return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st);
+  }
   // one CTA per SM with all 512 TMEM columns: measured faster at L = 3 than
   // two CTAs with 256 columns each (narrower N = 32 tiles, 2-stage rings)
   constexpr int TMEM = 512;
@@ -854,22 +868,28 @@ int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t
                    int prec, void* ws, size_t ws_bytes, cudaStream_t st) {
   if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3) return WP_ERR_UNSUPPORTED;
   if (L < 1 || L > 5) return WP_ERR_UNSUPPORTED;
-  if ((p >> L) > 65535 || n1 > INT32_MAX || n2 > INT32_MAX || n4 > INT32_MAX) return WP_ERR_UNSUPPORTED;
+  if ((p >> L) > 65535 || p > 65535 || n1 > INT32_MAX || n2 > INT32_MAX || n4 > INT32_MAX) return WP_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
   const int64_t Kp = pad8(n2);
   const bool x3 = (prec == WP_PREC_BF16X3);
+  // The inverse-lift epilogue needs all 2^L accumulators of a tile in TMEM,
+  // so its tile is only 512 / 2^L wide; when that would re-read A more than
+  // four times, keep the wide-tile GEMM and inverse-lift in a separate pass.
+  const int64_t bn_fused = 512 >> L;
+  const bool epilogue_fused = (n4 + bn_fused - 1) / bn_fused <= 4;
   Carver cv(ws, ws_bytes);
+  float* Chat = epilogue_fused ? nullptr : cv.take<float>(size_t(p) * n1 * n4);
   __nv_bfloat16* Ah = cv.take<__nv_bfloat16>(size_t(p) * n1 * Kp);
   __nv_bfloat16* Bh = cv.take<__nv_bfloat16>(size_t(p) * n4 * Kp);
   __nv_bfloat16* Al = x3 ? cv.take<__nv_bfloat16>(size_t(p) * n1 * Kp) : nullptr;
   __nv_bfloat16* Bl = x3 ? cv.take<__nv_bfloat16>(size_t(p) * n4 * Kp) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   switch (L) {
-    case 1: return fused_levels<1>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
-    case 2: return fused_levels<2>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
-    case 3: return fused_levels<3>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
-    case 4: return fused_levels<4>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
-    default: return fused_levels<5>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, st);
+    case 1: return fused_levels<1>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, Chat, st);
+    case 2: return fused_levels<2>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, Chat, st);
+    case 3: return fused_levels<3>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, Chat, st);
+    case 4: return fused_levels<4>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, Chat, st);
+    default: return fused_levels<5>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, Chat, st);
   }
 }
 

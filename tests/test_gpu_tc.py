@@ -125,6 +125,7 @@ FUSED_CASES = [
     (32, 17, 64, 40, 4),        # one short M tile, BN = 32
     (64, 50, 96, 21, 5),        # BN = 16, two groups
     (16, 1, 1, 1, 4),           # degenerate
+    (32, 64, 64, 300, 4),       # wide output: the wide-tile GEMM + separate inverse lift
 ]
 
 
