@@ -178,6 +178,9 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
         if (lane == 0) norms[c] = s;
       }
       __syncthreads();
+      float nmax = 0.f;   // numerically zero columns are not rotated (see jacobi.cu)
+      for (int c = 0; c < n_pad; ++c) nmax = fmaxf(nmax, norms[c]);
+      const float negligible = nmax * float(m_len) * float(m_len) * 1.4210855e-14f;
       int rotated_sweep = 0;
       for (int k = 0; k < n_pad - 1; ++k) {
         int rotated = 0;
@@ -194,7 +197,7 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
           const float al = norms[ca], be = norms[cb];
-          if (g != 0.f && fabsf(g) > tol_eff * sqrtf(al * be)) {
+          if (g != 0.f && al > negligible && be > negligible && fabsf(g) > tol_eff * sqrtf(al * be)) {
             const float zeta = __fdividef(be - al, 2.f * g);
             const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
             const float cs = rsqrtf(fmaf(t, t, 1.f));

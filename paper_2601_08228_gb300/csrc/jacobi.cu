@@ -186,6 +186,13 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
     const float tol_eff = sweep < kStrictSweeps ? a.tol : 8.f * a.tol;
     exact_norms(buf);
     buf ^= 1;
+    // a column whose squared norm is below (m eps)^2 |X|_max^2 is numerically
+    // zero: its direction is rounding noise, so its pairs are not rotated
+    // (otherwise a rank-deficient slice would never converge)
+    float nmax = 0.f;
+    for (int c = 0; c < n_pad; ++c) nmax = fmaxf(nmax, norms[c]);
+    const float meps = float(a.m_len) * 1.1920929e-7f;
+    const float negligible = nmax * meps * meps;
     int rotated_sweep = 0;
     for (int k = 0; k < n_pad - 1; ++k) {
       int rotated = 0;
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
           pair_of(im, k, n_pad, xa, xb);
           const float g = gather<CL>(part, buf, n_pad, im);
           const float al = norms[xa], be = norms[xb];
-          if (g != 0.f && fabsf(g) > tol_eff * sqrtf(al * be)) {
+          if (g != 0.f && al > negligible && be > negligible && fabsf(g) > tol_eff * sqrtf(al * be)) {
             // stable angle; c^2 + s^2 = 1 holds whatever the rounding of t
             const float zeta = __fdividef(be - al, 2.f * g);
             const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));

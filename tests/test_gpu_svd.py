@@ -122,6 +122,25 @@ def test_wsvd_hsi_256x256x192(r):
     assert capi.wp_get_device_error() == 0
 
 
+def test_rank_deficient_slices_converge():
+    """Collinear and zero columns (rank-deficient wavelet-domain slices) must
+    not keep the Jacobi sweeps rotating rounding noise: no NOT_CONVERGED."""
+    p, L, n = 8, 3, 24
+    rng = np.random.default_rng(21)
+    Ah = np.einsum("kir,krj->kij", rng.standard_normal((p, n, 3)), rng.standard_normal((p, 3, n)))
+    Ah[:, :, 5] = Ah[:, :, 4]            # duplicated column
+    Ah[:, :, 7] = 0.0                    # zero column
+    A = O.ilift(Ah, L).astype(np.float32)
+    capi.wp_get_device_error()
+    C = host(capi.wp_wsvd(dev(A), L, 3))
+    assert O.rel_fro(C, O.wsvd(A, L, 3)) <= 1e-4
+    # FP32 rounding leaves noise singular values ~1e-7 sigma_1 in the rank-3
+    # slices: compare at the GPU's cut-off max(m, n) eps_32, not the FP64 one
+    X = host(capi.wp_wpinv(dev(A), L))
+    assert O.rel_fro(X, O.wpinv(A, L, rtol=n * 1.1920929e-7)) <= 1e-3
+    assert capi.wp_get_device_error() == 0
+
+
 def test_wsvd_rank_errors():
     A = torch.zeros((8, 4, 6), device="cuda")
     for r in (0, 5):
