@@ -66,6 +66,18 @@ def dist_info():
     return ws, rank, local
 
 
+def reduce_max(values, device=None):
+    """Element-wise MAX of a list of floats over all ranks (identity when not
+    distributed): the step time of a weak-scaling run is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def inputs(np_dtype=np.float32):
     from paper_2601_08228_gb300 import synth
     w = WORKLOAD
@@ -312,10 +324,7 @@ def run_ours(args):
     t_wsvd = sum(e[1].elapsed_time(e[2]) for e in events) / 1e3 if have_wsvd else 0.0
     t_sp = sum(e[2].elapsed_time(e[3]) for e in events) / 1e3 if have_wsvd else 0.0
     t_step = t_prod + t_wsvd + t_sp
-    if ws > 1:
-        tt = torch.tensor([t_prod, t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_prod, t_step = tt.tolist()
+    t_prod, t_step = reduce_max([t_prod, t_step], device="cuda")
     value = ws * args.steps * wprod_flops() / t_prod / 1e12
 
     # FP32 comparison loop (same protocol), and errors against the oracle
