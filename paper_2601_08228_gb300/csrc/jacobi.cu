@@ -335,24 +335,19 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
 // In the round-robin ordering every element except position 0 moves one
 // position along the ring per round.  Warp w owns the PPW consecutive pairs
 // [w PPW, (w+1) PPW) and keeps the first 32 RPL of its CTA's rows of their
-// 2 PPW columns in registers for a whole sweep; per round only one column
-// leaves for each neighbouring warp, through a small shared-memory mailbox.
-// The CTA's remaining rows (if any) stay in shared memory indexed by column
-// id, so they never move: dot products and rotations combine both parts.
-// After n - 1 rounds the arrangement is back to the start.  With the rows of
-// a 256 x 256 slice split 128 / 128 between registers and shared memory, one
-// CTA holds a whole slice and a round needs no cluster barrier.
+// 2 PPW columns in registers for a whole sweep (all of the CTA's rows: at
+// most 32 RPL); per round only one column leaves for each neighbouring warp,
+// through a small shared-memory mailbox.  After n - 1 rounds the arrangement
+// is back to the start.  Shared memory holds only the staging of the input,
+// the partial sums, the norms and the mailboxes.
 template <int CL, int PPW, int RPL>
 __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs a) {
   static_assert(PPW >= 2, "ring kernel needs at least two pairs per warp");
   extern __shared__ float sm[];
   const int n_pad = a.n_pad, rpc = a.rpc;
-  constexpr int REGROWS = 32 * RPL;
-  const int regrows = rpc < REGROWS ? rpc : REGROWS;  // rows [0, regrows) in registers
-  const int srows = rpc - regrows;                    // rows [regrows, rpc) in shared memory
-  const int stage_ld = regrows > srows ? regrows : srows;
-  float* Xs = sm;                                     // [n_pad][srows] (after staging)
-  float* norms = Xs + size_t(n_pad) * stage_ld;       // [n_pad]
+  const int regrows = rpc;                            // <= 32 RPL: every row in registers
+  float* Xs = sm;                                     // [n_pad][rpc] input staging
+  float* norms = Xs + size_t(n_pad) * rpc;            // [n_pad]
   float* part = norms + n_pad;                        // [2][CL][n_pad]
   int* order = reinterpret_cast<int*>(part + 2 * CL * n_pad);   // [n_pad]
   int* rank_of = order + n_pad;                                 // [n_pad]
@@ -370,18 +365,14 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
   const int nw_used = n_pad / (2 * PPW);
   const bool active = warp < nw_used;
 
-  auto load_rows = [&](int first, int count) {       // rows [first, first+count) -> Xs [n_pad][count]
-    for (int idx = threadIdx.x; idx < n_pad * count; idx += JAC_THREADS) {
-      const int c = idx / count, rr = idx % count, R = row0 + first + rr;
-      float v = 0.f;
-      if (c < a.n_vec && R < a.m_len) v = a.trans ? A[int64_t(c) * a.n2 + R] : A[int64_t(R) * a.n2 + c];
-      Xs[idx] = v;
-    }
-  };
-
-  // stage the register rows through shared memory, then the shared-memory rows
+  // stage the CTA's rows through shared memory (coalesced), then into registers
+  for (int idx = threadIdx.x; idx < n_pad * rpc; idx += JAC_THREADS) {
+    const int c = idx / rpc, rr = idx % rpc, R = row0 + rr;
+    float v = 0.f;
+    if (c < a.n_vec && R < a.m_len) v = a.trans ? A[int64_t(c) * a.n2 + R] : A[int64_t(R) * a.n2 + c];
+    Xs[idx] = v;
+  }
   float T[PPW][RPL], B[PPW][RPL];
-  load_rows(0, regrows);
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < PPW; ++j) {
@@ -395,8 +386,6 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
     }
   }
   __syncthreads();
-  if (srows > 0) load_rows(regrows, srows);
-  __syncthreads();
 
   auto publish = [&](int buf, float total, int entry) {
     for (int q = lane & (LPP - 1); q < CL; q += LPP) {
@@ -404,12 +393,6 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
       if constexpr (CL == 1) *local = total;
       else *cg::this_cluster().map_shared_rank(local, q) = total;
     }
-  };
-  auto smem_sq = [&](int c) {                         // partial |x_c|^2 over the shared-memory rows
-    float s = 0.f;
-    const float* col = Xs + size_t(c) * srows;
-    for (int rr = lane; rr < srows; rr += 32) s = fmaf(col[rr], col[rr], s);
-    return s;
   };
 
   int buf = 0;
@@ -423,16 +406,11 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
       float nt[PPW], nb[PPW];
 #pragma unroll
       for (int j = 0; j < PPW; ++j) {
-        const int i = warp * PPW + j;
         nt[j] = nb[j] = 0.f;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
           nt[j] = fmaf(T[j][q], T[j][q], nt[j]);
           nb[j] = fmaf(B[j][q], B[j][q], nb[j]);
-        }
-        if (srows > 0 && active) {
-          nt[j] += smem_sq(i);
-          nb[j] += smem_sq(n_pad - 1 - i);
         }
       }
       const float tt = multi_reduce<PPW>(nt, lane);
@@ -456,21 +434,12 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
       // the registers move positions p -> p + 1 around the ring, i.e. the
       // circle schedule run backwards: round k holds the arrangement of -k
       const int kk = (k == 0) ? 0 : n_pad - 1 - k;
-      int ca[PPW], cb[PPW];
       float acc[PPW];
 #pragma unroll
       for (int j = 0; j < PPW; ++j) {
-        pair_of(warp * PPW + j, kk, n_pad, ca[j], cb[j]);
         acc[j] = 0.f;
 #pragma unroll
         for (int q = 0; q < RPL; ++q) acc[j] = fmaf(T[j][q], B[j][q], acc[j]);
-      }
-      if (srows > 0 && active) {
-        for (int rr = lane; rr < srows; rr += 32) {
-#pragma unroll
-          for (int j = 0; j < PPW; ++j)
-            acc[j] = fmaf(Xs[size_t(ca[j]) * srows + rr], Xs[size_t(cb[j]) * srows + rr], acc[j]);
-        }
       }
       const float tot = multi_reduce<PPW>(acc, lane);
       const int im = warp * PPW + (lane >> SHIFT);
@@ -505,17 +474,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
           T[j][q] = fmaf(c, u, -s * v);
           B[j][q] = fmaf(s, u, c * v);
         }
-        if (srows > 0 && active && s != 0.f) {
-          float* xa = Xs + size_t(ca[j]) * srows;
-          float* xb = Xs + size_t(cb[j]) * srows;
-          for (int rr = lane; rr < srows; rr += 32) {
-            const float u = xa[rr], v = xb[rr];
-            xa[rr] = fmaf(c, u, -s * v);
-            xb[rr] = fmaf(s, u, c * v);
-          }
-        }
       }
-      // ring move of the register rows: post the outgoing columns, then shift
+      // ring move: post the outgoing columns, then shift
       if (active) {
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
@@ -568,21 +528,16 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
     atomicMax(&a.stats[1], (unsigned long long)sweeps_done);
   }
 
-  // exact final norms (registers + shared memory), ranks, leading vectors
+  // exact final norms, ranks, leading vectors
   {
     float nt[PPW], nb[PPW];
 #pragma unroll
     for (int j = 0; j < PPW; ++j) {
-      const int i = warp * PPW + j;
       nt[j] = nb[j] = 0.f;
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         nt[j] = fmaf(T[j][q], T[j][q], nt[j]);
         nb[j] = fmaf(B[j][q], B[j][q], nb[j]);
-      }
-      if (srows > 0 && active) {
-        nt[j] += smem_sq(i);
-        nb[j] += smem_sq(n_pad - 1 - i);
       }
     }
     const float tt = multi_reduce<PPW>(nt, lane);
@@ -629,13 +584,6 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs 
         }
       }
     }
-  }
-  for (int idx = threadIdx.x; idx < a.r * srows; idx += JAC_THREADS) {
-    const int kq = idx / srows, rr = idx % srows, R = row0 + regrows + rr;
-    if (R >= a.m_len) continue;
-    const int c = order[kq];
-    const float sg = sqrtf(norms[c]);
-    vo[int64_t(R) * a.r + kq] = sg > 0.f ? Xs[size_t(c) * srows + rr] / sg : 0.f;
   }
   if (rank == 0)
     for (int kq = threadIdx.x; kq < a.r; kq += JAC_THREADS)
@@ -709,9 +657,7 @@ static int launch_jacobi_lg(const JacobiArgs& args, int nslices, size_t smem, cu
 }
 
 static size_t ring_smem(int n_pad, int rpc, int CL, int rpl) {
-  const int regrows = std::min(rpc, 32 * rpl), srows = rpc - regrows;
-  const int stage_ld = std::max(regrows, srows);
-  return (size_t(n_pad) * stage_ld + n_pad + 2 * size_t(CL) * n_pad) * sizeof(float) +
+  return (size_t(n_pad) * rpc + n_pad + 2 * size_t(CL) * n_pad) * sizeof(float) +
          2 * size_t(n_pad) * sizeof(int) + size_t(2) * (JAC_THREADS / 32) * rpl * 32 * sizeof(float);
 }
 
@@ -791,25 +737,23 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
       const int rpl_max = std::min(4, 32 / ppw);
       // measured on 256 x 256 slices: all rows in registers on a 2-CTA cluster
       // (~2.2 us per round) beats one CTA holding half the rows in shared
-      // memory (~4 us per round), so prefer full register residency and fall
-      // back to the split layout only when no cluster size allows it
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int CL = 1; CL <= 8; CL *= 2) {
-          const int rpc = (a.m_len + CL - 1) / CL;
-          int rpl_p2 = 1;
-          while (rpl_p2 < rpl_max && 32 * rpl_p2 < rpc) rpl_p2 *= 2;
-          if (pass == 0 && 32 * rpl_p2 < rpc) continue;
-          const size_t smem = ring_smem(n_ring, rpc, CL, rpl_p2);
-          if (smem > JAC_SMEM_MAX + 16 * 1024) continue;
-          JacobiArgs b = a;
-          b.n_pad = n_ring;
-          b.rpc = rpc;
-          switch (CL) {
-            case 1: return launch_ring_ppw<1>(b, nslices, smem, ppw, rpl_p2, st);
-            case 2: return launch_ring_ppw<2>(b, nslices, smem, ppw, rpl_p2, st);
-            case 4: return launch_ring_ppw<4>(b, nslices, smem, ppw, rpl_p2, st);
-            default: return launch_ring_ppw<8>(b, nslices, smem, ppw, rpl_p2, st);
-          }
+      // memory (~4 us per round): use the smallest cluster whose per-CTA rows
+      // all fit in registers, else the shared-memory kernel below
+      for (int CL = 1; CL <= 8; CL *= 2) {
+        const int rpc = (a.m_len + CL - 1) / CL;
+        int rpl_p2 = 1;
+        while (rpl_p2 < rpl_max && 32 * rpl_p2 < rpc) rpl_p2 *= 2;
+        if (32 * rpl_p2 < rpc) continue;
+        const size_t smem = ring_smem(n_ring, rpc, CL, rpl_p2);
+        if (smem > JAC_SMEM_MAX + 16 * 1024) continue;
+        JacobiArgs b = a;
+        b.n_pad = n_ring;
+        b.rpc = rpc;
+        switch (CL) {
+          case 1: return launch_ring_ppw<1>(b, nslices, smem, ppw, rpl_p2, st);
+          case 2: return launch_ring_ppw<2>(b, nslices, smem, ppw, rpl_p2, st);
+          case 4: return launch_ring_ppw<4>(b, nslices, smem, ppw, rpl_p2, st);
+          default: return launch_ring_ppw<8>(b, nslices, smem, ppw, rpl_p2, st);
         }
       }
     }
