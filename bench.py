@@ -582,7 +582,8 @@ def run_profile_case(case):
         A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
         capi.wp_wprod(A, B, WORKLOAD["L"], prec="bf16x3")
     elif case == "jacobi":
-        A = torch.from_numpy(synth.hsi_cube(256, 256, 16, seed=0, dtype=np.float32)).cuda()
+        # 72 slices of 256 x 256: 2-CTA clusters as in the full workload, one wave
+        A = torch.from_numpy(synth.hsi_cube(256, 256, 72, seed=0, dtype=np.float32)).cuda()
         capi.wp_wsvd(A, 3, 20)
     elif case == "batched":
         items = synth.batch_items(count=64, seed=1)

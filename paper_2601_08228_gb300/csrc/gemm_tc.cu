@@ -545,9 +545,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += CH) {
         if (n0 + c0 >= N) break;
+        // all G loads of the chunk in flight, then one wait
+        uint32_t raw[G * CH];
+#pragma unroll
+        for (int t = 0; t < G; ++t) ptx::tmem_ld_cols_async<CH>(lane_base + uint32_t(t * BN + c0), raw + t * CH);
+        ptx::tmem_wait_regs<G * CH>(raw);
         float v[G][CH];
 #pragma unroll
-        for (int t = 0; t < G; ++t) ptx::tmem_ld_cols<CH>(lane_base + uint32_t(t * BN + c0), v[t]);
+        for (int t = 0; t < G; ++t)
+#pragma unroll
+          for (int j = 0; j < CH; ++j) v[t][j] = __uint_as_float(raw[t * CH + j]);
         if (row < M) {
           // inverse transform across the group's G slices, column by column
 #pragma unroll

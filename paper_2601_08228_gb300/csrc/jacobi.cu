@@ -32,85 +32,11 @@
 // GB300 the FP64 pipe is ~64x slower than FP32, and the angle, being
 // computed from FP32 inputs, gains nothing measurable from FP64.
 
-#include <cooperative_groups.h>
-
 #include "common.cuh"
 #include "internal.cuh"
-
-namespace cg = cooperative_groups;
+#include "jacobi_common.cuh"
 
 namespace wp {
-
-constexpr int JAC_THREADS = 512;
-constexpr int kStrictSweeps = 20;
-
-struct JacobiArgs {
-  const float* X;      // slices (p, n1, n2)
-  int n1, n2;
-  int trans;           // 1: working columns are the rows of the slice
-  int m_len, n_vec, n_pad, rpc;
-  int slice0;          // first slice handled by this launch
-  int r;
-  float* vec_out;      // (p, m_len, r): leading r unit vectors, slice-indexed
-  float* sig_out;      // (p, r): leading r singular values, descending
-  float tol;
-  int max_sweeps;
-  int* status;
-  unsigned long long* stats;   // [0] += sweeps of each slice, [1] = max sweeps
-};
-
-__device__ __forceinline__ void pair_of(int i, int k, int n, int& a, int& b) {
-  // circle method: position 0 fixed, positions 1..n-1 rotate by k
-  auto elem = [&](int pos) {
-    int q = pos - 1 + k;
-    q -= (q >= n - 1) ? (n - 1) : 0;
-    return pos == 0 ? 0 : 1 + q;
-  };
-  a = elem(i);
-  b = elem(n - 1 - i);
-}
-
-template <int CL>
-__device__ __forceinline__ void cluster_barrier() {
-  if constexpr (CL > 1) cg::this_cluster().sync();
-  else __syncthreads();
-}
-
-template <int CL>
-__device__ __forceinline__ float gather(const float* part, int buf, int n_pad, int i) {
-  float s = 0.f;
-#pragma unroll
-  for (int q = 0; q < CL; ++q) s += part[(size_t(buf) * CL + q) * n_pad + i];
-  return s;
-}
-
-// Sum PPW per-lane values over the 32 lanes of a warp with a multi-value
-// butterfly: after the call, lane l holds the warp total of value
-// (l >> (5 - log2 PPW)).  log2(PPW) + (5 - log2 PPW) shuffle stages, 2 PPW - 1
-// + (5 - log2 PPW) shuffles in all (9 for PPW = 8, instead of 40).
-template <int PPW>
-__device__ __forceinline__ float multi_reduce(float (&v)[PPW], int lane) {
-  int c = PPW;
-  int d = 16;
-#pragma unroll
-  for (int step = 0; (1 << step) < PPW; ++step) {
-    c >>= 1;
-    const bool upper = (lane & d) != 0;
-#pragma unroll
-    for (int i = 0; i < PPW / 2; ++i) {
-      if (i < c) {
-        const float send = upper ? v[i] : v[i + c];
-        const float keep = upper ? v[i + c] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
-      }
-    }
-    d >>= 1;
-  }
-  float t = v[0];
-#pragma unroll
-  for (; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
-  return t;
-}
 
 // One warp owns PPW column pairs of a round; its 32 lanes sweep consecutive
 // rows (conflict-free shared-memory access) and the PPW pairs form
@@ -727,36 +653,10 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
   a.max_sweeps = 40;
   a.status = device_status_ptr();
   a.stats = jacobi_stats_ptr();
-  // register-resident ring kernel: more than 16 pairs per round, 2 PPW RPL <= 64
+  // block-cyclic register-resident kernel where the slice shape suits it
   {
-    const int npairs = a.n_pad / 2;
-    int ppw = 2;
-    while (ppw < 16 && 16 * ppw < npairs) ppw *= 2;
-    if (npairs > 16 && 16 * ppw >= npairs) {
-      const int n_ring = (a.n_pad + 2 * ppw - 1) / (2 * ppw) * (2 * ppw);
-      const int rpl_max = std::min(4, 32 / ppw);
-      // measured on 256 x 256 slices: all rows in registers on a 2-CTA cluster
-      // (~2.2 us per round) beats one CTA holding half the rows in shared
-      // memory (~4 us per round): use the smallest cluster whose per-CTA rows
-      // all fit in registers, else the shared-memory kernel below
-      for (int CL = 1; CL <= 8; CL *= 2) {
-        const int rpc = (a.m_len + CL - 1) / CL;
-        int rpl_p2 = 1;
-        while (rpl_p2 < rpl_max && 32 * rpl_p2 < rpc) rpl_p2 *= 2;
-        if (32 * rpl_p2 < rpc) continue;
-        const size_t smem = ring_smem(n_ring, rpc, CL, rpl_p2);
-        if (smem > JAC_SMEM_MAX + 16 * 1024) continue;
-        JacobiArgs b = a;
-        b.n_pad = n_ring;
-        b.rpc = rpc;
-        switch (CL) {
-          case 1: return launch_ring_ppw<1>(b, nslices, smem, ppw, rpl_p2, st);
-          case 2: return launch_ring_ppw<2>(b, nslices, smem, ppw, rpl_p2, st);
-          case 4: return launch_ring_ppw<4>(b, nslices, smem, ppw, rpl_p2, st);
-          default: return launch_ring_ppw<8>(b, nslices, smem, ppw, rpl_p2, st);
-        }
-      }
-    }
+    const int rc = jacobi_block_launch(a, nslices, st);
+    if (rc != WP_ERR_UNSUPPORTED) return rc;
   }
   const int CL = pick_cluster(a.m_len, a.n_pad, nslices);
   if (CL < 0) return WP_ERR_UNSUPPORTED;

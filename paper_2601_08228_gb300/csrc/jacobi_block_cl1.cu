@@ -1,0 +1,4 @@
+// Cluster size 1 instances of the block-cyclic Jacobi kernel.
+#include "jacobi_block.cuh"
+
+WP_JACOBI_BLOCK_INSTANTIATE(1)
