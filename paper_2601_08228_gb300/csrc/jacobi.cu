@@ -11,8 +11,14 @@
 // U) or its transpose otherwise (giving V); the other factor and the rank-r
 // reconstruction are recovered afterwards with small products (svd.cu).
 //
-// Parallel ordering: round-robin "circle" tournament, n_pad - 1 rounds of
-// n_pad / 2 disjoint pairs per sweep.  A slice is held in shared memory,
+// Two kernels share these definitions.  The block-cyclic register-resident
+// kernel (jacobi_block.cu) takes every slice with more than 32 columns whose
+// rows fit in registers on at most 8 CTAs; the shared-memory kernel below
+// takes the rest (narrow slices, very tall ones).
+//
+// Shared-memory kernel.  Parallel ordering: round-robin "circle" tournament,
+// n_pad - 1 rounds of n_pad / 2 disjoint pairs per sweep.  A slice is held in
+// shared memory,
 // split by rows across a thread-block cluster of CL CTAs (CL = 1, 2, 4, 8);
 // each warp computes its pairs' partial dot products over the CTA's rows, and publishes the partial to every CTA of
 // the cluster through distributed shared memory (double-buffered per round,
@@ -256,267 +262,6 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacobiArgs a) {
   cluster_barrier<CL>();
 }
 
-// ---- register-resident ring variant ----------------------------------------------------
-//
-// In the round-robin ordering every element except position 0 moves one
-// position along the ring per round.  Warp w owns the PPW consecutive pairs
-// [w PPW, (w+1) PPW) and keeps the first 32 RPL of its CTA's rows of their
-// 2 PPW columns in registers for a whole sweep (all of the CTA's rows: at
-// most 32 RPL); per round only one column leaves for each neighbouring warp,
-// through a small shared-memory mailbox.  After n - 1 rounds the arrangement
-// is back to the start.  Shared memory holds only the staging of the input,
-// the partial sums, the norms and the mailboxes.
-template <int CL, int PPW, int RPL>
-__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_ring_kernel(JacobiArgs a) {
-  static_assert(PPW >= 2, "ring kernel needs at least two pairs per warp");
-  extern __shared__ float sm[];
-  const int n_pad = a.n_pad, rpc = a.rpc;
-  const int regrows = rpc;                            // <= 32 RPL: every row in registers
-  float* Xs = sm;                                     // [n_pad][rpc] input staging
-  float* norms = Xs + size_t(n_pad) * rpc;            // [n_pad]
-  float* part = norms + n_pad;                        // [2][CL][n_pad]
-  int* order = reinterpret_cast<int*>(part + 2 * CL * n_pad);   // [n_pad]
-  int* rank_of = order + n_pad;                                 // [n_pad]
-  constexpr int NW = JAC_THREADS / 32;
-  float* mbox_top = reinterpret_cast<float*>(rank_of + n_pad);  // [NW][RPL * 32]
-  float* mbox_bot = mbox_top + NW * RPL * 32;                   // [NW][RPL * 32]
-  constexpr int LPP = 32 / PPW;
-  constexpr int SHIFT = (PPW == 2) ? 4 : (PPW == 4) ? 3 : (PPW == 8) ? 2 : 1;
-
-  const int rank = (CL > 1) ? int(cg::this_cluster().block_rank()) : 0;
-  const int slice = a.slice0 + int(blockIdx.x) / CL;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const float* A = a.X + int64_t(slice) * a.n1 * a.n2;
-  const int row0 = rank * rpc;
-  const int nw_used = n_pad / (2 * PPW);
-  const bool active = warp < nw_used;
-
-  // stage the CTA's rows through shared memory (coalesced), then into registers
-  for (int idx = threadIdx.x; idx < n_pad * rpc; idx += JAC_THREADS) {
-    const int c = idx / rpc, rr = idx % rpc, R = row0 + rr;
-    float v = 0.f;
-    if (c < a.n_vec && R < a.m_len) v = a.trans ? A[int64_t(c) * a.n2 + R] : A[int64_t(R) * a.n2 + c];
-    Xs[idx] = v;
-  }
-  float T[PPW][RPL], B[PPW][RPL];
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < PPW; ++j) {
-    const int i = warp * PPW + j;
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const int rr = lane + 32 * q;
-      const bool in = active && rr < regrows;
-      T[j][q] = in ? Xs[size_t(i) * regrows + rr] : 0.f;
-      B[j][q] = in ? Xs[size_t(n_pad - 1 - i) * regrows + rr] : 0.f;
-    }
-  }
-  __syncthreads();
-
-  auto publish = [&](int buf, float total, int entry) {
-    for (int q = lane & (LPP - 1); q < CL; q += LPP) {
-      float* local = part + (size_t(buf) * CL + rank) * n_pad + entry;
-      if constexpr (CL == 1) *local = total;
-      else *cg::this_cluster().map_shared_rank(local, q) = total;
-    }
-  };
-
-  int buf = 0;
-  bool converged = false;
-  int sweeps_done = 0;
-  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
-    sweeps_done = sweep + 1;
-    const float tol_eff = sweep < kStrictSweeps ? a.tol : 8.f * a.tol;
-    {
-      // exact column norms (arrangement is the initial one)
-      float nt[PPW], nb[PPW];
-#pragma unroll
-      for (int j = 0; j < PPW; ++j) {
-        nt[j] = nb[j] = 0.f;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          nt[j] = fmaf(T[j][q], T[j][q], nt[j]);
-          nb[j] = fmaf(B[j][q], B[j][q], nb[j]);
-        }
-      }
-      const float tt = multi_reduce<PPW>(nt, lane);
-      const float tb = multi_reduce<PPW>(nb, lane);
-      if (active) {
-        const int i = warp * PPW + (lane >> SHIFT);
-        publish(buf, tt, i);
-        publish(buf, tb, n_pad - 1 - i);
-      }
-      cluster_barrier<CL>();
-      for (int c = threadIdx.x; c < n_pad; c += JAC_THREADS) norms[c] = gather<CL>(part, buf, n_pad, c);
-      __syncthreads();
-      buf ^= 1;
-    }
-    float nmax = 0.f;
-    for (int c = 0; c < n_pad; ++c) nmax = fmaxf(nmax, norms[c]);
-    const float meps = float(a.m_len) * 1.1920929e-7f;
-    const float negligible = nmax * meps * meps;
-    int rotated_sweep = 0;
-    for (int k = 0; k < n_pad - 1; ++k) {
-      // the registers move positions p -> p + 1 around the ring, i.e. the
-      // circle schedule run backwards: round k holds the arrangement of -k
-      const int kk = (k == 0) ? 0 : n_pad - 1 - k;
-      float acc[PPW];
-#pragma unroll
-      for (int j = 0; j < PPW; ++j) {
-        acc[j] = 0.f;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) acc[j] = fmaf(T[j][q], B[j][q], acc[j]);
-      }
-      const float tot = multi_reduce<PPW>(acc, lane);
-      const int im = warp * PPW + (lane >> SHIFT);
-      if (active) publish(buf, tot, im);
-      cluster_barrier<CL>();
-      float cm = 1.f, sm_ = 0.f;
-      int rotated = 0;
-      if (active) {
-        int xa, xb;
-        pair_of(im, kk, n_pad, xa, xb);
-        const float g = gather<CL>(part, buf, n_pad, im);
-        const float al = norms[xa], be = norms[xb];
-        if (g != 0.f && al > negligible && be > negligible && fabsf(g) > tol_eff * sqrtf(al * be)) {
-          const float zeta = __fdividef(be - al, 2.f * g);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-          cm = rsqrtf(fmaf(t, t, 1.f));
-          sm_ = cm * t;
-          rotated = 1;
-          if ((lane & (LPP - 1)) == 0) {
-            norms[xa] = fmaf(-t, g, al);
-            norms[xb] = fmaf(t, g, be);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < PPW; ++j) {
-        const float c = __shfl_sync(0xffffffffu, cm, j << SHIFT);
-        const float s = __shfl_sync(0xffffffffu, sm_, j << SHIFT);
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          const float u = T[j][q], v = B[j][q];
-          T[j][q] = fmaf(c, u, -s * v);
-          B[j][q] = fmaf(s, u, c * v);
-        }
-      }
-      // ring move: post the outgoing columns, then shift
-      if (active) {
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          if (warp + 1 < nw_used) mbox_top[warp * RPL * 32 + q * 32 + lane] = T[PPW - 1][q];
-          if (warp > 0) mbox_bot[warp * RPL * 32 + q * 32 + lane] = B[0][q];
-        }
-      }
-      rotated_sweep |= __syncthreads_or(rotated);
-      if (active) {
-        float oldT[RPL], oldB[RPL];
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          oldT[q] = T[PPW - 1][q];
-          oldB[q] = B[0][q];
-        }
-#pragma unroll
-        for (int j = PPW - 1; j >= 2; --j)
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) T[j][q] = T[j - 1][q];
-        if (warp == 0) {
-          // position 0 stays; position 1 receives the element from position n - 1
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) T[1][q] = oldB[q];
-        } else {
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) {
-            T[1][q] = T[0][q];
-            T[0][q] = mbox_top[(warp - 1) * RPL * 32 + q * 32 + lane];
-          }
-        }
-#pragma unroll
-        for (int j = 0; j + 1 < PPW; ++j)
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) B[j][q] = B[j + 1][q];
-        if (warp == nw_used - 1) {
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) B[PPW - 1][q] = oldT[q];
-        } else {
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) B[PPW - 1][q] = mbox_bot[(warp + 1) * RPL * 32 + q * 32 + lane];
-        }
-      }
-      buf ^= 1;
-    }
-    if (!rotated_sweep) { converged = true; break; }
-  }
-  if (!converged && threadIdx.x == 0 && rank == 0) report_device_error(a.status, WP_ERR_NOT_CONVERGED);
-  if (threadIdx.x == 0 && rank == 0 && a.stats) {
-    atomicAdd(&a.stats[0], (unsigned long long)sweeps_done);
-    atomicMax(&a.stats[1], (unsigned long long)sweeps_done);
-  }
-
-  // exact final norms, ranks, leading vectors
-  {
-    float nt[PPW], nb[PPW];
-#pragma unroll
-    for (int j = 0; j < PPW; ++j) {
-      nt[j] = nb[j] = 0.f;
-#pragma unroll
-      for (int q = 0; q < RPL; ++q) {
-        nt[j] = fmaf(T[j][q], T[j][q], nt[j]);
-        nb[j] = fmaf(B[j][q], B[j][q], nb[j]);
-      }
-    }
-    const float tt = multi_reduce<PPW>(nt, lane);
-    const float tb = multi_reduce<PPW>(nb, lane);
-    if (active) {
-      const int i = warp * PPW + (lane >> SHIFT);
-      publish(buf, tt, i);
-      publish(buf, tb, n_pad - 1 - i);
-    }
-    cluster_barrier<CL>();
-    for (int c = threadIdx.x; c < n_pad; c += JAC_THREADS) norms[c] = gather<CL>(part, buf, n_pad, c);
-    __syncthreads();
-  }
-  for (int c = threadIdx.x; c < n_pad; c += JAC_THREADS) {
-    int pos = a.r;
-    if (c < a.n_vec) {
-      const float sc = norms[c];
-      pos = 0;
-      for (int q = 0; q < a.n_vec; ++q) {
-        const float sq = norms[q];
-        pos += (sq > sc) || (sq == sc && q < c);
-      }
-      if (pos < a.r) order[pos] = c;
-    }
-    rank_of[c] = pos < a.r ? pos : -1;
-  }
-  __syncthreads();
-  float* vo = a.vec_out + int64_t(slice) * a.m_len * a.r;
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < PPW; ++j) {
-      const int i = warp * PPW + j;
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int c = side ? n_pad - 1 - i : i;
-        const int kq = rank_of[c];
-        if (kq < 0) continue;
-        const float sg = sqrtf(norms[c]);
-        const float inv = sg > 0.f ? 1.f / sg : 0.f;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          const int R = row0 + lane + 32 * q;
-          if (lane + 32 * q < regrows && R < a.m_len) vo[int64_t(R) * a.r + kq] = (side ? B[j][q] : T[j][q]) * inv;
-        }
-      }
-    }
-  }
-  if (rank == 0)
-    for (int kq = threadIdx.x; kq < a.r; kq += JAC_THREADS)
-      a.sig_out[int64_t(slice) * a.r + kq] = sqrtf(norms[order[kq]]);
-  cluster_barrier<CL>();
-}
-
 static size_t jacobi_smem(int n_pad, int rpc, int CL) {
   return (size_t(n_pad) * rpc + n_pad + 2 * size_t(CL) * n_pad) * sizeof(float) + size_t(n_pad) * sizeof(int);
 }
@@ -580,54 +325,6 @@ static int launch_jacobi_lg(const JacobiArgs& args, int nslices, size_t smem, cu
   if (npairs <= 2 * nw) return launch_jacobi_rpl<CL, 2>(args, nslices, smem, st);
   if (npairs <= 4 * nw) return launch_jacobi_rpl<CL, 4>(args, nslices, smem, st);
   return launch_jacobi_rpl<CL, 8>(args, nslices, smem, st);
-}
-
-static size_t ring_smem(int n_pad, int rpc, int CL, int rpl) {
-  return (size_t(n_pad) * rpc + n_pad + 2 * size_t(CL) * n_pad) * sizeof(float) +
-         2 * size_t(n_pad) * sizeof(int) + size_t(2) * (JAC_THREADS / 32) * rpl * 32 * sizeof(float);
-}
-
-template <int CL, int PPW, int RPL>
-static int launch_ring(const JacobiArgs& args, int nslices, size_t smem, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    WP_CUDA_TRY(cudaFuncSetAttribute(jacobi_ring_kernel<CL, PPW, RPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(JAC_SMEM_MAX + 24 * 1024)));
-    attr = true;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(nslices * CL), 1, 1);
-  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attrs[1];
-  attrs[0].id = cudaLaunchAttributeClusterDimension;
-  attrs[0].val.clusterDim.x = CL;
-  attrs[0].val.clusterDim.y = 1;
-  attrs[0].val.clusterDim.z = 1;
-  cfg.attrs = attrs;
-  cfg.numAttrs = 1;
-  WP_PROFILE("jacobi_svd", st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_ring_kernel<CL, PPW, RPL>, args));
-  return launch_status();
-}
-
-template <int CL, int PPW>
-static int launch_ring_rpl(const JacobiArgs& a, int nslices, size_t smem, int rpl, cudaStream_t st) {
-  if (rpl == 1) return launch_ring<CL, PPW, 1>(a, nslices, smem, st);
-  if (rpl == 2) return launch_ring<CL, PPW, 2>(a, nslices, smem, st);
-  if constexpr (PPW <= 8) return launch_ring<CL, PPW, 4>(a, nslices, smem, st);
-  return WP_ERR_UNSUPPORTED;
-}
-
-template <int CL>
-static int launch_ring_ppw(const JacobiArgs& a, int nslices, size_t smem, int ppw, int rpl, cudaStream_t st) {
-  switch (ppw) {
-    case 2: return launch_ring_rpl<CL, 2>(a, nslices, smem, rpl, st);
-    case 4: return launch_ring_rpl<CL, 4>(a, nslices, smem, rpl, st);
-    case 8: return launch_ring_rpl<CL, 8>(a, nslices, smem, rpl, st);
-    default: return launch_ring_rpl<CL, 16>(a, nslices, smem, rpl, st);
-  }
 }
 
 // Leading r singular triplets of slices [slice0, slice0 + nslices) of X
