@@ -35,6 +35,9 @@
 #include "lift_math.cuh"
 #include "tc_ptx.cuh"
 
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
 namespace wp {
 
 // ---- operand preparation ---------------------------------------------------------
@@ -449,13 +452,23 @@ struct FusedLayout {
   static constexpr int CH = 64 / G < 16 ? 64 / G : 16;  // columns per epilogue chunk (registers: G * CH = 64)
 };
 
-template <int L, int NPROD, int STAGES, int TMEM>
+// MC > 1: the MC CTAs of a cluster (consecutive N tiles of one row tile and
+// tube group) share every A tile: each fetches BM / MC of its rows and
+// multicasts them to all, and a stage is refilled only after all MC CTAs
+// have consumed it (their MMA commits arrive on every CTA's `empty`).
+// BMN: B is MN-major -- W(B) in its natural (K rows, N contiguous) layout,
+// loaded as 64-column boxes -- instead of K-major.
+template <int L, int NPROD, int STAGES, int TMEM, int MC, bool BMN>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_ilift_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                          const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                          float* __restrict__ C, int M, int N, int K, int64_t p, int* status) {
   using Lay = FusedLayout<L, NPROD, STAGES, TMEM>;
   constexpr int G = Lay::G, BN = Lay::BN, CH = Lay::CH;
+  static_assert(!BMN || BN % 64 == 0, "MN-major B needs 64-column blocks");
+  static_assert(BM % MC == 0, "A rows split over the cluster");
+  constexpr int AR = BM / MC;                                  // A rows fetched by this CTA
+  constexpr uint16_t MASK = uint16_t((1u << MC) - 1u);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFF);
@@ -477,7 +490,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], 1);
+      ptx::mbar_init(&empty[s], MC);
     }
     ptx::mbar_init(accum, 1);
     ptx::fence_mbar_init();
@@ -486,7 +499,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
+  // every CTA's barriers are initialised before any peer multicasts into it
+  if constexpr (MC > 1) cg::this_cluster().sync();
   const uint32_t tmem = *tmem_slot;
+  const int crank = (MC > 1) ? int(cg::this_cluster().block_rank()) : 0;
   bool ok = true;
 
   if (warp == 0 && lane == 0) {
@@ -500,10 +516,24 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (it >= STAGES) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
       if (!ok) break;
       ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
-      ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BK, m0, z, &full[s]);
-      if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BK, m0, z, &full[s]);
-      ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BK, n0, z, &full[s]);
-      if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BK, n0, z, &full[s]);
+      if constexpr (MC > 1) {
+        ptx::tma_load_3d_mc(a_tile(s, 0) + crank * AR * 128, &tmAh, kb * BK, m0 + crank * AR, z, &full[s], MASK);
+        if (NPROD == 3)
+          ptx::tma_load_3d_mc(a_tile(s, 1) + crank * AR * 128, &tmAl, kb * BK, m0 + crank * AR, z, &full[s], MASK);
+      } else {
+        ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BK, m0, z, &full[s]);
+        if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BK, m0, z, &full[s]);
+      }
+      if constexpr (BMN) {
+#pragma unroll
+        for (int j = 0; j < BN / 64; ++j) {
+          ptx::tma_load_3d(b_tile(s, 0) + j * 8192, &tmBh, n0 + 64 * j, kb * BK, z, &full[s]);
+          if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1) + j * 8192, &tmBl, n0 + 64 * j, kb * BK, z, &full[s]);
+        }
+      } else {
+        ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BK, n0, z, &full[s]);
+        if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BK, n0, z, &full[s]);
+      }
       ++issued;
     }
     if (!ok) {
@@ -511,7 +541,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         ptx::mbar_wait(&full[it % STAGES], (it / STAGES) & 1, nullptr, 100000000ull);
     }
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
+    constexpr uint32_t idesc = BMN ? ptx::idesc_bf16_f32_bmn(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
+    // B descriptor of K step kk: K-major advances 32 bytes along the row,
+    // MN-major 16 rows of 128 bytes
+    auto bdesc = [&](int s, int copy, int kk) {
+      if constexpr (BMN) return ptx::sdesc_mnmajor_sw128(b_tile(s, copy) + kk * 2048, 8192);
+      else return ptx::sdesc_kmajor_sw128(b_tile(s, copy) + kk * 32);
+    };
     for (int it = 0; it < iters && ok; ++it) {
       const int s = it % STAGES;
       const int t = it / nk, kb = it % nk;
@@ -522,16 +558,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint64_t ah = ptx::sdesc_kmajor_sw128(a_tile(s, 0) + kk * 32);
-        const uint64_t bh = ptx::sdesc_kmajor_sw128(b_tile(s, 0) + kk * 32);
+        const uint64_t bh = bdesc(s, 0, kk);
         ptx::mma_bf16(d, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
         if (NPROD == 3) {
           const uint64_t al = ptx::sdesc_kmajor_sw128(a_tile(s, 1) + kk * 32);
-          const uint64_t bl = ptx::sdesc_kmajor_sw128(b_tile(s, 1) + kk * 32);
+          const uint64_t bl = bdesc(s, 1, kk);
           ptx::mma_bf16(d, ah, bl, idesc, 1u);
           ptx::mma_bf16(d, al, bh, idesc, 1u);
         }
       }
-      ptx::mma_commit(&empty[s]);
+      if constexpr (MC > 1) ptx::mma_commit_mc(&empty[s], MASK);
+      else ptx::mma_commit(&empty[s]);
     }
     ptx::mma_commit(accum);
   } else if (warp >= 2) {
@@ -596,6 +633,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
     ptx::tmem_dealloc(tmem, TMEM);
   }
+  // no CTA leaves while a peer's multicast or commit can still reach it
+  if constexpr (MC > 1) cg::this_cluster().sync();
 }
 
 }  // namespace tc
@@ -810,27 +849,46 @@ static int launch_lift_split_rows(const float* A, __nv_bfloat16* hi, __nv_bfloat
   return launch_status();
 }
 
-// TMEM = 256 halves the tile width so that two CTAs (each with its own
-// 256 TMEM columns and < 113 KB of shared memory) share an SM; TMEM = 512
-// keeps one CTA per SM with the widest tile.
-template <int L, int NPROD, int TMEM>
+// One CTA per SM with all 512 TMEM columns (measured faster at L = 3 than
+// two CTAs with 256 columns each: narrower N = 32 tiles, 2-stage rings).
+// MC: CTAs of a cluster sharing A tiles by multicast (consecutive N tiles).
+template <int L, int NPROD, int MC, bool BMN>
 static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                         float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st) {
+  constexpr int TMEM = 512;
   using Probe = tc::FusedLayout<L, NPROD, 1, TMEM>;
-  constexpr int BUDGET = (TMEM == 512) ? 196608 : 110592;
-  constexpr int STAGES = std::min(6, BUDGET / Probe::STAGE);
+  constexpr int STAGES = std::min(6, 196608 / Probe::STAGE);
   using Lay = tc::FusedLayout<L, NPROD, STAGES, TMEM>;
+  auto kern = tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM, MC, BMN>;
   static bool attr = false;
   if (!attr) {
-    WP_CUDA_TRY(cudaFuncSetAttribute(tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
+    WP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
     attr = true;
   }
-  const dim3 grid{unsigned((N + Lay::BN - 1) / Lay::BN), unsigned((M + tc::BM - 1) / tc::BM), unsigned(p >> L)};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned((N + Lay::BN - 1) / Lay::BN), unsigned((M + tc::BM - 1) / tc::BM), unsigned(p >> L));
+  cfg.blockDim = dim3(tc::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Lay::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = MC;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
   WP_PROFILE(NPROD == 3 ? "tc_gemm_ilift_bf16x3" : "tc_gemm_ilift_bf16", st);
-  tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM><<<grid, tc::THREADS, Lay::SMEM, st>>>(
-      ah, al, bh, bl, C, int(M), int(N), int(K), p, device_status_ptr());
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, C, int(M), int(N), int(K), p, device_status_ptr()));
   return launch_status();
+}
+
+template <int L, int NPROD, bool BMN>
+static int launch_fused_mc(int mc, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
+                           const CUtensorMap& bl, float* C, int64_t M, int64_t N, int64_t K, int64_t p,
+                           cudaStream_t st) {
+  if (mc == 4) return launch_fused<L, NPROD, 4, BMN>(ah, al, bh, bl, C, M, N, K, p, st);
+  if (mc == 2) return launch_fused<L, NPROD, 2, BMN>(ah, al, bh, bl, C, M, N, K, p, st);
+  return launch_fused<L, NPROD, 1, BMN>(ah, al, bh, bl, C, M, N, K, p, st);
 }
 
 template <int L>
@@ -838,10 +896,10 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
                         bool x3, __nv_bfloat16* Ah, __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl,
                         int64_t Kp, float* Chat, cudaStream_t st) {
   WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
-  WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
   CUtensorMap mah, mal, mbh, mbl;
   if (Chat) {
     // wide-tile GEMM into the wavelet-domain C_hat, then the inverse transform
+    WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
     WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
     if (x3) {
       WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, tc::BM));
@@ -854,18 +912,27 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
     }
     return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st);
   }
-  // one CTA per SM with all 512 TMEM columns: measured faster at L = 3 than
-  // two CTAs with 256 columns each (narrower N = 32 tiles, 2-stage rings)
-  constexpr int TMEM = 512;
-  constexpr int BN = tc::FusedLayout<L, 1, 1, TMEM>::BN;
-  WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
-  WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, BN));
-  if (x3) {
-    WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, tc::BM));
-    WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, BN));
-    return launch_fused<L, 3, TMEM>(mah, mal, mbh, mbl, C, n1, n4, n2, p, st);
+  constexpr int BN = tc::FusedLayout<L, 1, 1, 512>::BN;
+  constexpr bool BMN = (L <= 3);
+  // A tiles shared by the cluster's N tiles: as many CTAs as divide the N tiles (at most 4)
+  const int64_t ntiles = (n4 + BN - 1) / BN;
+  const int mc = (ntiles % 4 == 0) ? 4 : (ntiles % 2 == 0) ? 2 : 1;
+  const int arows = tc::BM / mc;
+  WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, arows));
+  if (x3) WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, arows));
+  if constexpr (BMN) {
+    // W(B) in its natural layout (K rows of n4 columns), 64-column boxes
+    const int64_t Np = pad8(n4);
+    WP_TRY(launch_lift_split_rows<L>(B, Bh, Bl, p, int(n2), int(n4), int(Np), st));
+    WP_TRY(make_map(&mbh, Bh, n4, Np, n2, p, tc::BK));
+    if (x3) WP_TRY(make_map(&mbl, Bl, n4, Np, n2, p, tc::BK));
+  } else {
+    WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
+    WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, BN));
+    if (x3) WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, BN));
   }
-  return launch_fused<L, 1, TMEM>(mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
+  if (x3) return launch_fused_mc<L, 3, BMN>(mc, mah, mal, mbh, mbl, C, n1, n4, n2, p, st);
+  return launch_fused_mc<L, 1, BMN>(mc, mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
 }
 
 // C = A *w B for tensor-core precisions with the transform fused into the
@@ -886,10 +953,13 @@ int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t
   const bool epilogue_fused = (n4 + bn_fused - 1) / bn_fused <= 4;
   Carver cv(ws, ws_bytes);
   float* Chat = epilogue_fused ? nullptr : cv.take<float>(size_t(p) * n1 * n4);
+  // B operand: (p, n2, pad8(n4)) MN-major on the fused-epilogue path at
+  // L <= 3, else (p, n4, Kp) K-major; room for the larger of the two
+  const size_t bsz = size_t(p) * std::max<int64_t>(n4 * Kp, n2 * pad8(n4));
   __nv_bfloat16* Ah = cv.take<__nv_bfloat16>(size_t(p) * n1 * Kp);
-  __nv_bfloat16* Bh = cv.take<__nv_bfloat16>(size_t(p) * n4 * Kp);
+  __nv_bfloat16* Bh = cv.take<__nv_bfloat16>(bsz);
   __nv_bfloat16* Al = x3 ? cv.take<__nv_bfloat16>(size_t(p) * n1 * Kp) : nullptr;
-  __nv_bfloat16* Bl = x3 ? cv.take<__nv_bfloat16>(size_t(p) * n4 * Kp) : nullptr;
+  __nv_bfloat16* Bl = x3 ? cv.take<__nv_bfloat16>(bsz) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   switch (L) {
     case 1: return fused_levels<1>(A, B, C, n1, n2, n4, p, x3, Ah, Al, Bh, Bl, Kp, Chat, st);

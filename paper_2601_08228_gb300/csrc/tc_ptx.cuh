@@ -88,6 +88,39 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
       : "memory");
 }
 
+// As tma_load_3d, but the box lands at the same shared-memory offset in every
+// CTA of the cluster named in cta_mask, each signalled on its own `bar`.
+__device__ __forceinline__ void tma_load_3d_mc(void* smem_dst, const CUtensorMap* map, int x, int y, int z,
+                                               uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+// 3-D tiled store of one box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* smem_src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(z), "r"(smem_u32(smem_src))
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until the committed bulk stores have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Wait until the committed bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Order this thread's generic-proxy shared-memory writes before later
+// async-proxy (TMA) reads of them.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ---- tcgen05 ------------------------------------------------------------------
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -123,6 +156,21 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(const void* smem_tile) {
   return d;
 }
 
+// Shared-memory matrix descriptor: MN-major operand tile stored as 128-byte
+// rows along MN (64 BF16) with consecutive rows consecutive in K, 128-byte
+// swizzle; 8-row K groups 1024 bytes apart (stride byte offset), 64-element
+// MN blocks `mn_block_bytes` apart (leading byte offset).
+__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(const void* smem_tile, uint32_t mn_block_bytes) {
+  const uint64_t addr = smem_u32(smem_tile);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;                            // start address (16-byte units)
+  d |= uint64_t((mn_block_bytes >> 4) & 0x3FFF) << 16;     // leading byte offset: next 64-wide MN block
+  d |= uint64_t(1024 >> 4) << 32;                          // stride byte offset: next 8 K rows
+  d |= uint64_t(1) << 46;                                  // descriptor version for tcgen05
+  d |= uint64_t(2) << 61;                                  // layout: SWIZZLE_128B
+  return d;
+}
+
 // Instruction descriptor for kind::f16 with BF16 A and B (both K-major) and
 // an FP32 accumulator, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
@@ -132,6 +180,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | (uint32_t(N >> 3) << 17)
          | (uint32_t(M >> 4) << 24);
 }
+
+// As idesc_bf16_f32, with B MN-major (bit 16: B transposed).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_bmn(int M, int N) { return idesc_bf16_f32(M, N) | (1u << 16); }
 
 // Instruction descriptor for kind::f8f6f4 with E4M3 A and B (both K-major)
 // and an FP32 accumulator, shape M x N.
@@ -173,6 +224,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(bar))
                : "memory");
+}
+
+// As mma_commit, arriving on the barrier at the same offset in every CTA of
+// the cluster named in cta_mask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(cta_mask)
+      : "memory");
 }
 
 // tcgen05.wait::ld that also takes the loaded registers as in/out operands,
