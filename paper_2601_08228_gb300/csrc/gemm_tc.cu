@@ -438,6 +438,14 @@ __global__ void __launch_bounds__(256) lift_split_transpose_kernel(const float* 
 
 namespace tc {
 
+// Slices per store pass of the fused epilogue: the largest power of two <= G
+// whose 128 x BN FP32 tiles fit in `bytes` of staging memory (0: none fit).
+__host__ __device__ constexpr int fused_store_slices(int G, int BN, int bytes) {
+  int s = G;
+  while (s > 0 && s * 128 * BN * 4 > bytes) s >>= 1;
+  return s;
+}
+
 template <int L, int NPROD, int STAGES, int TMEM = 512>
 struct FusedLayout {
   static constexpr int G = 1 << L;
@@ -462,9 +470,15 @@ template <int L, int NPROD, int STAGES, int TMEM, int MC, bool BMN>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_ilift_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                          const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                         float* __restrict__ C, int M, int N, int K, int64_t p, int* status) {
+                         const __grid_constant__ CUtensorMap tmC, int tma_store, float* __restrict__ C, int M,
+                         int N, int K, int64_t p, int* status) {
   using Lay = FusedLayout<L, NPROD, STAGES, TMEM>;
   constexpr int G = Lay::G, BN = Lay::BN, CH = Lay::CH;
+  // TMA-store epilogue: the output tiles of SPP slices are staged in the
+  // (then idle) pipeline buffers as 32-column blocks of 128-byte rows with
+  // the 128-byte swizzle, and written by one 3-D bulk store per block
+  constexpr bool TMA_EPI = (BN >= 32) && (CH >= 4);
+  constexpr int SPP = fused_store_slices(G, BN, STAGES * Lay::STAGE);
   static_assert(!BMN || BN % 64 == 0, "MN-major B needs 64-column blocks");
   static_assert(BM % MC == 0, "A rows split over the cluster");
   constexpr int AR = BM / MC;                                  // A rows fetched by this CTA
@@ -574,35 +588,76 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp >= 2) {
     ok = ptx::mbar_wait(accum, 0, status);
     ptx::tc_fence_after();
-    if (ok) {
-      const int quad = warp & 3;
-      const int row = m0 + quad * 32 + lane;
-      const uint32_t lane_base = tmem + (uint32_t(quad * 32) << 16);
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;   // row within the tile
+    const int row = m0 + r;
+    const uint32_t lane_base = tmem + (uint32_t(quad * 32) << 16);
+    // columns [c0, c0 + CH) of all G accumulators, inverse-transformed across
+    // the group's G slices (Eq. 3): v[t][j] = spatial slice t, column c0 + j
+    auto load_chunk = [&](int c0, float (&v)[G][CH]) {
+      uint32_t raw[G * CH];   // all G loads in flight, then one wait
+#pragma unroll
+      for (int t = 0; t < G; ++t) ptx::tmem_ld_cols_async<CH>(lane_base + uint32_t(t * BN + c0), raw + t * CH);
+      ptx::tmem_wait_regs<G * CH>(raw);
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        float y[G], x[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) y[t] = __uint_as_float(raw[t * CH + j]);
+        ilift_group<L>(y, x);
+#pragma unroll
+        for (int t = 0; t < G; ++t) v[t][j] = x[t];
+      }
+    };
+    if (TMA_EPI && SPP >= 1 && tma_store) {
+      if constexpr (TMA_EPI && SPP >= 1) {
+        const bool leader = (warp == 2 && lane == 0);
+        auto epi_sync = [] { asm volatile("bar.sync 1, 128;" ::: "memory"); };
+#pragma unroll
+        for (int pass = 0; pass < G / SPP; ++pass) {
+          if (pass > 0) {
+            // the previous pass's stores have read the staging buffers
+            if (leader) ptx::bulk_wait_read_all();
+            epi_sync();
+          }
+          if (ok) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += CH) {
+              if (n0 + c0 >= N) break;
+              float v[G][CH];
+              load_chunk(c0, v);
+              const int h = c0 / 32, q0 = (c0 % 32) / 4;
+#pragma unroll
+              for (int tt = 0; tt < SPP; ++tt) {
+                uint8_t* base = smem + (h * SPP + tt) * 16384 + r * 128;
+#pragma unroll
+                for (int k = 0; k < CH / 4; ++k) {
+                  const int t = pass * SPP + tt;
+                  *reinterpret_cast<float4*>(base + (((q0 + k) ^ (r & 7)) << 4)) =
+                      make_float4(v[t][4 * k], v[t][4 * k + 1], v[t][4 * k + 2], v[t][4 * k + 3]);
+                }
+              }
+            }
+          }
+          ptx::fence_proxy_async_smem();
+          epi_sync();
+          if (leader && ok) {
+#pragma unroll
+            for (int h = 0; h < BN / 32; ++h)
+              ptx::tma_store_3d(&tmC, smem + h * SPP * 16384, n0 + 32 * h, m0, int(g * G + pass * SPP));
+            ptx::bulk_commit();
+          }
+        }
+        if (leader) ptx::bulk_wait_all();
+      }
+    } else if (ok) {
       const bool vec = (N % 4) == 0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += CH) {
         if (n0 + c0 >= N) break;
-        // all G loads of the chunk in flight, then one wait
-        uint32_t raw[G * CH];
-#pragma unroll
-        for (int t = 0; t < G; ++t) ptx::tmem_ld_cols_async<CH>(lane_base + uint32_t(t * BN + c0), raw + t * CH);
-        ptx::tmem_wait_regs<G * CH>(raw);
         float v[G][CH];
-#pragma unroll
-        for (int t = 0; t < G; ++t)
-#pragma unroll
-          for (int j = 0; j < CH; ++j) v[t][j] = __uint_as_float(raw[t * CH + j]);
+        load_chunk(c0, v);
         if (row < M) {
-          // inverse transform across the group's G slices, column by column
-#pragma unroll
-          for (int j = 0; j < CH; ++j) {
-            float y[G], x[G];
-#pragma unroll
-            for (int t = 0; t < G; ++t) y[t] = v[t][j];
-            ilift_group<L>(y, x);
-#pragma unroll
-            for (int t = 0; t < G; ++t) v[t][j] = x[t];
-          }
           const int col = n0 + c0;
 #pragma unroll
           for (int t = 0; t < G; ++t) {
@@ -667,6 +722,22 @@ static int make_map(CUtensorMap* map, const void* base, int64_t K, int64_t Kp, i
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType dt = (esize == 2) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? WP_OK : WP_ERR_CUDA;
+}
+
+// Tensor map of an FP32 (batch, rows, cols) array, box bx x by x bz with the
+// 128-byte swizzle (bx * 4 = 128 bytes), for tiled stores.
+static int make_map_f32(CUtensorMap* map, const float* base, int64_t cols, int64_t rows, int64_t batch, int bx,
+                        int by, int bz) {
+  auto fn = encode_fn();
+  if (!fn) return WP_ERR_CUDA;
+  cuuint64_t dims[3] = {cuuint64_t(cols), cuuint64_t(rows), cuuint64_t(batch)};
+  cuuint64_t strides[2] = {cuuint64_t(cols * 4), cuuint64_t(rows * cols * 4)};
+  cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), cuuint32_t(bz)};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? WP_OK : WP_ERR_CUDA;
@@ -877,8 +948,18 @@ static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUte
   attrs[0].val.clusterDim.z = 1;
   cfg.attrs = attrs;
   cfg.numAttrs = 1;
+  // output tensor map for the TMA-store epilogue: (p, M, N) FP32 with N % 4
+  // == 0 (16-byte row stride), boxes of 32 columns x 128 rows x SPP slices
+  constexpr int SPP = tc::fused_store_slices(Lay::G, Lay::BN, STAGES * Lay::STAGE);
+  CUtensorMap mc = ah;
+  int tma_store = 0;
+  if (Lay::BN >= 32 && Lay::CH >= 4 && SPP >= 1 && N % 4 == 0 && aligned16(C)) {
+    WP_TRY(make_map_f32(&mc, C, N, M, p, 32, tc::BM, SPP));
+    tma_store = 1;
+  }
   WP_PROFILE(NPROD == 3 ? "tc_gemm_ilift_bf16x3" : "tc_gemm_ilift_bf16", st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, C, int(M), int(N), int(K), p, device_status_ptr()));
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, mc, tma_store, C, int(M), int(N), int(K), p,
+                                 device_status_ptr()));
   return launch_status();
 }
 
