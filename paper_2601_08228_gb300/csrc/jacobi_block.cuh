@@ -260,6 +260,9 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
   // squared norms held by lane group g: top column g, and the bottom column
   // currently paired with it ((g + s) mod PPW in column round s)
   float nT = 0.f, nB = 0.f;
+  // scales d of the same columns (stored y = x / d): the inter-block rounds
+  // defer each rotation's cosine into them; 1 again at every block move
+  float dT = 1.f, dB = 1.f;
   auto exact_norms = [&]() {
     float st[PPW], sb[PPW];
 #pragma unroll
@@ -296,6 +299,16 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
     s = 0.f;
     t = 0.f;
     return false;
+  };
+
+  // plane rotation with the cosine deferred to the column scales
+  auto shear = [&](float (&X)[RPL], float (&Y)[RPL], float ta, float tb) {
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const float u = X[q], v = Y[q];
+      X[q] = fmaf(-ta, v, u);
+      Y[q] = fmaf(tb, u, v);
+    }
   };
 
   auto rotate = [&](float (&X)[RPL], float (&Y)[RPL], float c, float s) {
@@ -393,26 +406,52 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
 #pragma unroll
             for (int q = 0; q < RPL; ++q) acc[j] = fmaf(T[j][q], B[(j + S) % PPW][q], acc[j]);
           }
-          const float gam = total(multi_reduce<PPW>(acc, lane));
-          float c, s, t;
+          // stored columns are x = d y: the dot product of the x's
+          const float gam = total(multi_reduce<PPW>(acc, lane)) * (dT * dB);
+          // scale ratios, off the angle's dependency chain
+          const float rba = __fdividef(dB, dT), rab = __fdividef(dT, dB);
+          float c, s, t, ta = 0.f, tb = 0.f;
           if (angle(gam, nT, nB, negl, tol2, c, s, t)) {
             nT = fmaf(-t, gam, nT);
             nB = fmaf(t, gam, nB);
             rot_any = 1;
+            // x_a' = c (x_a - t x_b), x_b' = c (x_b + t x_a) with the cosine
+            // moved into the scales: y_a -= t (d_b / d_a) y_b, y_b += t (d_a / d_b) y_a
+            ta = t * rba;
+            tb = t * rab;
+            dT *= c;
+            dB *= c;
           }
           // broadcast the PPW rotations through shared memory
           __syncwarp();
-          if (sub == 0) *reinterpret_cast<float2*>(cs_w + 2 * g) = make_float2(c, s);
+          if (sub == 0) *reinterpret_cast<float2*>(cs_w + 2 * g) = make_float2(ta, tb);
           __syncwarp();
 #pragma unroll
           for (int j = 0; j < PPW; j += 2) {
             const float4 r2 = *reinterpret_cast<const float4*>(cs_w + 2 * j);
-            if (r2.y != 0.f) rotate(T[j], B[(j + S) % PPW], r2.x, r2.y);
-            if (r2.w != 0.f) rotate(T[j + 1], B[(j + 1 + S) % PPW], r2.z, r2.w);
+            if (r2.x != 0.f) shear(T[j], B[(j + S) % PPW], r2.x, r2.y);
+            if (r2.z != 0.f) shear(T[j + 1], B[(j + 1 + S) % PPW], r2.z, r2.w);
           }
           // the bottom block advances one column relative to the top one
           nB = __shfl_sync(0xffffffffu, nB, (lane + LPP) & 31);
+          dB = __shfl_sync(0xffffffffu, dB, (lane + LPP) & 31);
         });
+      }
+      if (active) {
+        // fold the column scales into the stored rows (d = 1 again)
+        __syncwarp();
+        if (sub == 0) *reinterpret_cast<float2*>(cs_w + 2 * g) = make_float2(dT, dB);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < PPW; ++j) {
+          const float2 d = *reinterpret_cast<const float2*>(cs_w + 2 * j);
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            T[j][q] *= d.x;
+            B[j][q] *= d.y;
+          }
+        }
+        dT = dB = 1.f;
       }
       // block move: positions 1..nb-1 advance by one (position 0 stays):
       // top of warp w -> top of w + 1 (last warp: its own bottom), bottom of
