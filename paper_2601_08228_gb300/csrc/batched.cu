@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "jacobi_common.cuh"
 #include "lift_math.cuh"
 
 namespace wp {
@@ -156,7 +157,7 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
     const int n1 = it.n1, n2 = it.n2, r = it.r;
     const bool trans = n1 < n2;
     const int m_len = trans ? n2 : n1, n_vec = trans ? n1 : n2;
-    const int n_pad = std::max(2, n_vec + (n_vec & 1));
+    const int n_pad = (n_vec + (n_vec & 1)) < 2 ? 2 : (n_vec + (n_vec & 1));
     const int npairs = n_pad / 2;
     const float* A = it.Ah + int64_t(uk.y) * n1 * n2;
     const float tol = 2.f * sqrtf(float(max(m_len, 16))) * 1.1920929e-7f;
@@ -184,30 +185,67 @@ __global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int
       int rotated_sweep = 0;
       for (int k = 0; k < n_pad - 1; ++k) {
         int rotated = 0;
-        for (int i = warp; i < npairs; i += nwarps) {
-          int ca, cb;
-          circle_pair(i, k, n_pad, ca, cb);
-          float* xa = Xs + ca * m_len;
-          float* xb = Xs + cb * m_len;
-          // m_len <= 64: two rows per lane, kept in registers
-          const int r0 = lane, r1 = lane + 32;
-          const float u0 = r0 < m_len ? xa[r0] : 0.f, v0 = r0 < m_len ? xb[r0] : 0.f;
-          const float u1 = r1 < m_len ? xa[r1] : 0.f, v1 = r1 < m_len ? xb[r1] : 0.f;
-          float g = fmaf(u0, v0, u1 * v1);
+        // a warp takes up to 8 pairs of the round at once: pair j of the pass
+        // is i = base + warp + j * nwarps; lanes hold rows lane, lane + 32
+        for (int base = 0; base < npairs; base += 8 * nwarps) {
+          int ca[8], cb[8];
+          float u0[8], v0[8], u1[8], v1[8], acc[8];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-          const float al = norms[ca], be = norms[cb];
-          if (g != 0.f && al > negligible && be > negligible && fabsf(g) > tol_eff * sqrtf(al * be)) {
-            const float zeta = __fdividef(be - al, 2.f * g);
-            const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-            const float cs = rsqrtf(fmaf(t, t, 1.f));
-            const float sn = cs * t;
-            if (r0 < m_len) { xa[r0] = fmaf(cs, u0, -sn * v0); xb[r0] = fmaf(sn, u0, cs * v0); }
-            if (r1 < m_len) { xa[r1] = fmaf(cs, u1, -sn * v1); xb[r1] = fmaf(sn, u1, cs * v1); }
-            __syncwarp();
-            if (lane == 0) { norms[ca] = fmaf(-t, g, al); norms[cb] = fmaf(t, g, be); }
-            rotated = 1;
+          for (int j = 0; j < 8; ++j) {
+            const int i = base + warp + j * nwarps;
+            ca[j] = cb[j] = 0;
+            if (i < npairs) circle_pair(i, k, n_pad, ca[j], cb[j]);
+            const bool in = i < npairs;
+            const float* xa = Xs + ca[j] * m_len;
+            const float* xb = Xs + cb[j] * m_len;
+            u0[j] = (in && lane < m_len) ? xa[lane] : 0.f;
+            v0[j] = (in && lane < m_len) ? xb[lane] : 0.f;
+            u1[j] = (in && lane + 32 < m_len) ? xa[lane + 32] : 0.f;
+            v1[j] = (in && lane + 32 < m_len) ? xb[lane + 32] : 0.f;
+            acc[j] = fmaf(u0[j], v0[j], u1[j] * v1[j]);
           }
+          // lane group l >> 2 holds the total of pair (l >> 2)
+          const float g = multi_reduce<8>(acc, lane);
+          const int jm = lane >> 2;
+          const int im = base + warp + jm * nwarps;
+          float cm = 1.f, sm_ = 0.f;
+          if (im < npairs) {
+            int xa, xb;
+            circle_pair(im, k, n_pad, xa, xb);
+            const float al = norms[xa], be = norms[xb];
+            if (al > negligible && be > negligible && g * g > tol_eff * tol_eff * (al * be)) {
+              const float zeta = __fdividef(be - al, 2.f * g);
+              const float az = fminf(fabsf(zeta), 1e18f);
+              const float h = fmaf(az, az, 1.f);
+              const float t = copysignf(__fdividef(1.f, az + h * rsqrtf(h)), zeta);
+              cm = rsqrtf(fmaf(t, t, 1.f));
+              sm_ = cm * t;
+              rotated = 1;
+              if ((lane & 3) == 0) {
+                norms[xa] = fmaf(-t, g, al);
+                norms[xb] = fmaf(t, g, be);
+              }
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float c = __shfl_sync(0xffffffffu, cm, j << 2);
+            const float sn = __shfl_sync(0xffffffffu, sm_, j << 2);
+            if (sn != 0.f) {
+              float* xa = Xs + ca[j] * m_len;
+              float* xb = Xs + cb[j] * m_len;
+              if (lane < m_len) {
+                xa[lane] = fmaf(c, u0[j], -sn * v0[j]);
+                xb[lane] = fmaf(sn, u0[j], c * v0[j]);
+              }
+              if (lane + 32 < m_len) {
+                xa[lane + 32] = fmaf(c, u1[j], -sn * v1[j]);
+                xb[lane + 32] = fmaf(sn, u1[j], c * v1[j]);
+              }
+            }
+          }
+          // the next pass of this round reads other columns; the next round
+          // waits at the barrier below
         }
         rotated_sweep |= __syncthreads_or(rotated);
       }
