@@ -9,8 +9,9 @@
 //                   chunks of (tube group, plane range), L dispatched per chunk)
 //   2. face-product every wavelet-domain slice A_hat_k B_hat_k (one slice per
 //                   CTA iteration, operands staged in shared memory)
-//   3. Jacobi SVD   every slice of A_hat (one-sided Jacobi in shared memory),
-//                   the rank-r slice C_hat_k = U_r U_r^T A_hat_k (or
+//   3. Jacobi SVD   every slice of A_hat (block-cyclic one-sided Jacobi, the
+//                   slice's columns in registers, jacobi_block.cuh), the
+//                   rank-r slice C_hat_k = U_r U_r^T A_hat_k (or
 //                   A_hat_k V_r V_r^T) rebuilt in the same CTA
 //   4. inverse lifting of every C_hat and C_hat_r
 // wp_batched_run performs no allocation, host synchronisation or copy, so it
@@ -21,6 +22,7 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "jacobi_block.cuh"
 #include "jacobi_common.cuh"
 #include "lift_math.cuh"
 
@@ -125,163 +127,50 @@ __global__ void batched_facewise_kernel(const BItem* __restrict__ items, const i
 
 // ---- phase 3: grouped Jacobi SVD + rank-r rebuild ---------------------------------------
 
-__device__ __forceinline__ void circle_pair(int i, int k, int n, int& a, int& b) {
-  auto elem = [&](int pos) {
-    int q = pos - 1 + k;
-    q -= (q >= n - 1) ? (n - 1) : 0;
-    return pos == 0 ? 0 : 1 + q;
-  };
-  a = elem(i);
-  b = elem(n - 1 - i);
-}
+// Jacobi phase: the block-cyclic register-resident one-sided Jacobi of
+// jacobi_block.cuh on one CTA per wavelet-domain slice (persistent over the
+// work list): blocks of PPW columns, NW warps, rows lane and lane + 32 of
+// every column in registers (slices up to 64 x 64), then the rank-r rebuild
+// from the leading vectors, staged in shared memory.
+template <int PPW, int NW>
+struct BJ {
+  static constexpr int RPL = 2;
+  static constexpr size_t BLOCK = jblock::block_smem<1, PPW, RPL, NW>(BMAX);   // n_pad <= 64
+  static constexpr size_t SMEM = BLOCK + size_t(BMAX) * BMAX * sizeof(float);  // + leading vectors
+};
 
-// shared memory layout per CTA: Xs [64][64] (column-major, stride m_len),
-// reused for T once the leading vectors are extracted; vec [64][64]
-// (m_len x r); norms [64]
-constexpr int JB_SMEM_FLOATS = BMAX * BMAX * 2 + BMAX;
-
-__global__ void batched_jacobi_kernel(const BItem* __restrict__ items, const int2* __restrict__ units,
-                                      int64_t nunits, int max_sweeps, int* status,
-                                      unsigned long long* stats) {
-  __shared__ float sm[JB_SMEM_FLOATS];
-  __shared__ int order[BMAX];
-  float* Xs = sm;
-  float* vec = sm + BMAX * BMAX;
-  float* T = Xs;                       // after vec is built, Xs is free
-  float* norms = vec + BMAX * BMAX;
-  const int nthr = blockDim.x, nwarps = nthr >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+template <int PPW, int NW>
+__global__ void __launch_bounds__(NW * 32) batched_jacobi_kernel(const BItem* __restrict__ items,
+                                                                 const int2* __restrict__ units, int64_t nunits,
+                                                                 int max_sweeps, int* status,
+                                                                 unsigned long long* stats) {
+  using L = BJ<PPW, NW>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* vec = reinterpret_cast<float*>(smem_raw + L::BLOCK);   // m_len x r
+  float* T = reinterpret_cast<float*>(smem_raw);                // rebuild scratch (block area is free by then)
+  constexpr int nthr = NW * 32;
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int2 uk = units[u];
     const BItem it = items[uk.x];
     const int n1 = it.n1, n2 = it.n2, r = it.r;
-    const bool trans = n1 < n2;
-    const int m_len = trans ? n2 : n1, n_vec = trans ? n1 : n2;
-    const int n_pad = (n_vec + (n_vec & 1)) < 2 ? 2 : (n_vec + (n_vec & 1));
-    const int npairs = n_pad / 2;
+    JacobiArgs b{};
+    b.n1 = n1;
+    b.n2 = n2;
+    b.trans = (n1 < n2) ? 1 : 0;
+    b.m_len = b.trans ? n2 : n1;
+    b.n_vec = b.trans ? n1 : n2;
+    b.n_pad = (b.n_vec + 2 * PPW - 1) / (2 * PPW) * (2 * PPW);
+    b.rpc = b.m_len;
+    b.r = r;
+    b.tol = 2.f * sqrtf(float(b.m_len < 16 ? 16 : b.m_len)) * 1.1920929e-7f;
+    b.max_sweeps = max_sweeps;
+    b.status = status;
+    b.stats = stats;
     const float* A = it.Ah + int64_t(uk.y) * n1 * n2;
-    const float tol = 2.f * sqrtf(float(max(m_len, 16))) * 1.1920929e-7f;
-    for (int idx = threadIdx.x; idx < n_pad * m_len; idx += nthr) {
-      const int c = idx / m_len, R = idx % m_len;
-      Xs[idx] = (c < n_vec) ? (trans ? A[c * n2 + R] : A[R * n2 + c]) : 0.f;
-    }
-    __syncthreads();
-    bool converged = false;
-    int sweeps_done = 0;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-      sweeps_done = sweep + 1;
-      const float tol_eff = sweep < 20 ? tol : 8.f * tol;   // see jacobi.cu
-      for (int c = warp; c < n_pad; c += nwarps) {
-        float s = 0.f;
-        for (int R = lane; R < m_len; R += 32) s = fmaf(Xs[c * m_len + R], Xs[c * m_len + R], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) norms[c] = s;
-      }
-      __syncthreads();
-      float nmax = 0.f;   // numerically zero columns are not rotated (see jacobi.cu)
-      for (int c = 0; c < n_pad; ++c) nmax = fmaxf(nmax, norms[c]);
-      const float negligible = nmax * float(m_len) * float(m_len) * 1.4210855e-14f;
-      int rotated_sweep = 0;
-      for (int k = 0; k < n_pad - 1; ++k) {
-        int rotated = 0;
-        // a warp takes up to 8 pairs of the round at once: pair j of the pass
-        // is i = base + warp + j * nwarps; lanes hold rows lane, lane + 32
-        for (int base = 0; base < npairs; base += 8 * nwarps) {
-          int ca[8], cb[8];
-          float u0[8], v0[8], u1[8], v1[8], acc[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int i = base + warp + j * nwarps;
-            ca[j] = cb[j] = 0;
-            if (i < npairs) circle_pair(i, k, n_pad, ca[j], cb[j]);
-            const bool in = i < npairs;
-            const float* xa = Xs + ca[j] * m_len;
-            const float* xb = Xs + cb[j] * m_len;
-            u0[j] = (in && lane < m_len) ? xa[lane] : 0.f;
-            v0[j] = (in && lane < m_len) ? xb[lane] : 0.f;
-            u1[j] = (in && lane + 32 < m_len) ? xa[lane + 32] : 0.f;
-            v1[j] = (in && lane + 32 < m_len) ? xb[lane + 32] : 0.f;
-            acc[j] = fmaf(u0[j], v0[j], u1[j] * v1[j]);
-          }
-          // lane group l >> 2 holds the total of pair (l >> 2)
-          const float g = multi_reduce<8>(acc, lane);
-          const int jm = lane >> 2;
-          const int im = base + warp + jm * nwarps;
-          float cm = 1.f, sm_ = 0.f;
-          if (im < npairs) {
-            int xa, xb;
-            circle_pair(im, k, n_pad, xa, xb);
-            const float al = norms[xa], be = norms[xb];
-            if (al > negligible && be > negligible && g * g > tol_eff * tol_eff * (al * be)) {
-              const float zeta = __fdividef(be - al, 2.f * g);
-              const float az = fminf(fabsf(zeta), 1e18f);
-              const float h = fmaf(az, az, 1.f);
-              const float t = copysignf(__fdividef(1.f, az + h * rsqrtf(h)), zeta);
-              cm = rsqrtf(fmaf(t, t, 1.f));
-              sm_ = cm * t;
-              rotated = 1;
-              if ((lane & 3) == 0) {
-                norms[xa] = fmaf(-t, g, al);
-                norms[xb] = fmaf(t, g, be);
-              }
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float c = __shfl_sync(0xffffffffu, cm, j << 2);
-            const float sn = __shfl_sync(0xffffffffu, sm_, j << 2);
-            if (sn != 0.f) {
-              float* xa = Xs + ca[j] * m_len;
-              float* xb = Xs + cb[j] * m_len;
-              if (lane < m_len) {
-                xa[lane] = fmaf(c, u0[j], -sn * v0[j]);
-                xb[lane] = fmaf(sn, u0[j], c * v0[j]);
-              }
-              if (lane + 32 < m_len) {
-                xa[lane + 32] = fmaf(c, u1[j], -sn * v1[j]);
-                xb[lane + 32] = fmaf(sn, u1[j], c * v1[j]);
-              }
-            }
-          }
-          // the next pass of this round reads other columns; the next round
-          // waits at the barrier below
-        }
-        rotated_sweep |= __syncthreads_or(rotated);
-      }
-      if (!rotated_sweep) { converged = true; break; }
-    }
-    if (!converged && threadIdx.x == 0) report_device_error(status, WP_ERR_NOT_CONVERGED);
-    if (threadIdx.x == 0 && stats) {
-      atomicAdd(&stats[0], (unsigned long long)sweeps_done);
-      atomicMax(&stats[1], (unsigned long long)sweeps_done);
-    }
-    // exact norms, rank the columns, normalised leading vectors into vec (m_len x r)
-    for (int c = warp; c < n_pad; c += nwarps) {
-      float s = 0.f;
-      for (int R = lane; R < m_len; R += 32) s = fmaf(Xs[c * m_len + R], Xs[c * m_len + R], s);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) norms[c] = s;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n_vec; c += nthr) {
-      const float sc = norms[c];
-      int pos = 0;
-      for (int q = 0; q < n_vec; ++q) pos += (norms[q] > sc) || (norms[q] == sc && q < c);
-      if (pos < r) order[pos] = c;
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < m_len * r; idx += nthr) {
-      const int R = idx / r, kq = idx % r;
-      const int c = order[kq];
-      const float sg = sqrtf(norms[c]);
-      vec[idx] = sg > 0.f ? Xs[c * m_len + R] / sg : 0.f;
-    }
-    __syncthreads();
+    jblock::block_jacobi_slice<1, PPW, L::RPL, NW>(b, A, 0, vec, nullptr, smem_raw);
     // rebuild the rank-r slice from the original A_hat_k (still in global memory)
     float* Cr = it.Crh + int64_t(uk.y) * n1 * n2;
-    if (!trans) {
+    if (!b.trans) {
       // T = U^T A (r x n2), C = U T
       for (int idx = threadIdx.x; idx < r * n2; idx += nthr) {
         const int kq = idx / n2, j = idx % n2;
@@ -399,13 +288,28 @@ static int launch_batched_gemm(const BItem* items, const int2* units, int64_t n,
   return launch_status();
 }
 
-static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t n, int threads, cudaStream_t st) {
-  const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * (2048 / threads));
+template <int PPW, int NW>
+static int launch_batched_jacobi_t(const BItem* items, const int2* units, int64_t n, cudaStream_t st) {
+  using L = BJ<PPW, NW>;
+  static int per_sm = 0;
+  if (!per_sm) {
+    WP_CUDA_TRY(cudaFuncSetAttribute(batched_jacobi_kernel<PPW, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(L::SMEM)));
+    WP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_jacobi_kernel<PPW, NW>, NW * 32,
+                                                              L::SMEM));
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * per_sm);
   WP_PROFILE("batched_jacobi", st);
-  batched_jacobi_kernel<<<unsigned(std::max<int64_t>(grid, 1)), threads, 0, st>>>(items, units, n, 40,
-                                                                                  device_status_ptr(),
-                                                                                  jacobi_stats_ptr());
+  batched_jacobi_kernel<PPW, NW><<<unsigned(std::max<int64_t>(grid, 1)), NW * 32, L::SMEM, st>>>(
+      items, units, n, 40, device_status_ptr(), jacobi_stats_ptr());
   return launch_status();
+}
+
+// threads: 128 (4 warps, blocks of 8 columns) or 256 (8 warps, blocks of 4)
+static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t n, int threads, cudaStream_t st) {
+  if (threads == 256) return launch_batched_jacobi_t<4, 8>(items, units, n, st);
+  return launch_batched_jacobi_t<8, 4>(items, units, n, st);
 }
 
 // Time one candidate configuration of a phase (median of 3 runs).
@@ -504,7 +408,7 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
       if (t < best) { best = t; plan->gemm_threads = thr; }
     }
     best = 1e30f;
-    for (int thr : {64, 128, 256}) {
+    for (int thr : {128, 256}) {
       const float t = time_candidate([&] { launch_batched_jacobi(di, du, lay.nunits, thr, st); }, st);
       if (t < best) { best = t; plan->svd_threads = thr; }
     }

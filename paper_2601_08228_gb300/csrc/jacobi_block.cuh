@@ -117,18 +117,18 @@ __device__ __forceinline__ void load_row(const float* p, float (&x)[RPL]) {
 // warp maxima [NW] | block norms in transit [NW][2][PPW] | norms [n_pad] |
 // order [n_pad] | rank_of [n_pad] | (16-byte aligned) block mailboxes
 // [NW][2][PPW][32][RPL], which first stage the input slice.
-template <int CL, int PPW>
+template <int CL, int PPW, int NW = kBlockWarps>
 __host__ __device__ constexpr size_t block_mail_offset(int n_pad) {
-  return ((size_t(16) * kBlockWarps + sizeof(float) * size_t(kBlockWarps) * 2 * PPW +
-           sizeof(float) * (size_t(kBlockWarps) * 2 * CL * PPW + kBlockWarps + size_t(kBlockWarps) * 2 * PPW + n_pad) +
+  return ((size_t(16) * NW + sizeof(float) * size_t(NW) * 2 * PPW +
+           sizeof(float) * (size_t(NW) * 2 * CL * PPW + NW + size_t(NW) * 2 * PPW + n_pad) +
            sizeof(int) * 2 * size_t(n_pad)) +
           15) /
          16 * 16;
 }
 
-template <int CL, int PPW, int RPL>
-size_t block_smem(int n_pad) {
-  return block_mail_offset<CL, PPW>(n_pad) + sizeof(float) * size_t(n_pad) * 32 * RPL;
+template <int CL, int PPW, int RPL, int NW = kBlockWarps>
+__host__ __device__ constexpr size_t block_smem(int n_pad) {
+  return block_mail_offset<CL, PPW, NW>(n_pad) + sizeof(float) * size_t(n_pad) * 32 * RPL;
 }
 
 // Rank-ordered cluster total of a per-pair partial (lane group g holds pair
@@ -192,16 +192,22 @@ struct PeerSum {
   }
 };
 
-template <int CL, int PPW, int RPL>
-__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs a) {
+// One slice on a cluster of CL CTAs of NW warps: A is the slice (n1 x n2,
+// row-major), this CTA holds working rows [rank * rpc, (rank + 1) * rpc);
+// writes the leading r unit vectors to vo (m_len x r, row-major; any
+// memory space) and, from rank 0, the r singular values to so (if not
+// null).  smem_raw: block_smem<CL, PPW, RPL, NW>(a.n_pad) bytes.  Ends with a
+// cluster-wide barrier.
+template <int CL, int PPW, int RPL, int NW>
+__device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const float* A, int rank, float* vo,
+                                                   float* so, unsigned char* smem_raw) {
   static_assert(PPW >= 2 && PPW <= 16 && (PPW & (PPW - 1)) == 0, "PPW: 2, 4, 8 or 16");
   static_assert(2 * PPW * RPL <= 64, "register budget: 2 PPW RPL <= 64 values per lane");
-  constexpr int NW = kBlockWarps;
+  constexpr int NTH = NW * 32;
   constexpr int LPP = 32 / PPW;
   constexpr int SHIFT = (PPW == 2) ? 4 : (PPW == 4) ? 3 : (PPW == 8) ? 2 : 1;
   constexpr int HALF = PPW / 2;
   constexpr int BLK = PPW * RPL * 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n_pad = a.n_pad, rpc = a.rpc;
   const int nb = n_pad / PPW, nw = nb / 2;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);           // [NW][2]
@@ -212,20 +218,17 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
   float* norms = mnorm + NW * 2 * PPW;                              // [n_pad]
   int* order = reinterpret_cast<int*>(norms + n_pad);               // [n_pad]
   int* rank_of = order + n_pad;                                     // [n_pad]
-  float* mail = reinterpret_cast<float*>(smem_raw + block_mail_offset<CL, PPW>(n_pad));
+  float* mail = reinterpret_cast<float*>(smem_raw + block_mail_offset<CL, PPW, NW>(n_pad));
 
-  const int rank = (CL > 1) ? int(cg::this_cluster().block_rank()) : 0;
-  const int slice = a.slice0 + int(blockIdx.x) / CL;
   const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
   const int g = lane >> SHIFT, sub = lane & (LPP - 1);
   const bool active = warp < nw;
-  const float* A = a.X + int64_t(slice) * a.n1 * a.n2;
   const int row0 = rank * rpc;
   const int topc = warp * PPW, botc = (nb - 1 - warp) * PPW;
 
   // stage the CTA's rows of the working matrix, column-major, in the mailboxes
   float* Xs = mail;
-  for (int idx = threadIdx.x; idx < n_pad * rpc; idx += JAC_THREADS) {
+  for (int idx = threadIdx.x; idx < n_pad * rpc; idx += NTH) {
     const int c = idx / rpc, rr = idx % rpc, R = row0 + rr;
     float v = 0.f;
     if (c < a.n_vec && R < a.m_len) v = a.trans ? A[int64_t(c) * a.n2 + R] : A[int64_t(R) * a.n2 + c];
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
     }
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < n_pad; c += JAC_THREADS) {
+  for (int c = threadIdx.x; c < n_pad; c += NTH) {
     int pos = a.r;
     if (c < a.n_vec) {
       const float sc = norms[c];
@@ -521,7 +524,6 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
     rank_of[c] = pos < a.r ? pos : -1;
   }
   __syncthreads();
-  float* vo = a.vec_out + int64_t(slice) * a.m_len * a.r;
   if (active) {
 #pragma unroll
     for (int j = 0; j < PPW; ++j) {
@@ -540,11 +542,20 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs
       }
     }
   }
-  if (rank == 0)
-    for (int kq = threadIdx.x; kq < a.r; kq += JAC_THREADS)
-      a.sig_out[int64_t(slice) * a.r + kq] = sqrtf(norms[order[kq]]);
+  if (rank == 0 && so)
+    for (int kq = threadIdx.x; kq < a.r; kq += NTH) so[kq] = sqrtf(norms[order[kq]]);
   // no CTA may leave while a peer can still write into its shared memory
   cluster_barrier<CL>();
+}
+
+template <int CL, int PPW, int RPL>
+__global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rank = (CL > 1) ? int(cg::this_cluster().block_rank()) : 0;
+  const int slice = a.slice0 + int(blockIdx.x) / CL;
+  block_jacobi_slice<CL, PPW, RPL, kBlockWarps>(a, a.X + int64_t(slice) * a.n1 * a.n2, rank,
+                                                a.vec_out + int64_t(slice) * a.m_len * a.r,
+                                                a.sig_out + int64_t(slice) * a.r, smem_raw);
 }
 
 template <int CL, int PPW, int RPL>
