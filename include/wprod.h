@@ -153,6 +153,33 @@ WP_API int wp_wprod(const float* A, const float* B, float* C, int64_t n1, int64_
              int64_t p, int L, int transA, int transB, int prec, void* ws, size_t ws_bytes,
              void* stream);
 
+/* ---- w-product of host-resident tensors ---------------------------------- */
+
+/* C = A *w B (Def. 2.1, Algorithm 1; no transposes) for A (p, n1, n2),
+ * B (p, n2, n4) and C (p, n1, n4) in HOST memory.  The slices are taken in
+ * chunks of `chunk_slices` consecutive slices, a multiple of 2^L so that every
+ * chunk holds whole tube groups (the transform never mixes two groups, so
+ * each chunk's product is the product of its slices): chunk k + 1 is copied
+ * to the device while chunk k is multiplied (wp_wprod) and chunk k - 1 is
+ * copied back, on three library-owned streams that start after the work
+ * already queued on `stream`; `stream` then waits for the last copy back.
+ * The result equals wp_wprod's on the same slices.  chunk_slices = 0 picks
+ * about p / 4 (rounded up to a multiple of 2^L).
+ *   - Page-locked host buffers let the copies overlap; pageable ones work
+ *     but each copy then blocks the host.
+ *   - ws: device memory of wp_wprod_host_workspace() bytes (two chunks of A,
+ *     B and C, and one chunk's wp_wprod workspace), 256-byte aligned.
+ *   - All calls on one device share the three streams and their events:
+ *     calls from several host threads on one device must be serialised.
+ * Errors: as wp_wprod (shapes, levels, precision, workspace), WP_ERR_NULL
+ * for a null buffer, WP_ERR_SHAPE for a chunk that is not a multiple of 2^L,
+ * WP_ERR_CUDA when a copy or stream operation fails. */
+WP_API int wp_wprod_host_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
+                                   int64_t chunk_slices, size_t* bytes);
+WP_API int wp_wprod_host(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
+                         int64_t p, int L, int prec, int64_t chunk_slices, void* ws, size_t ws_bytes,
+                         void* stream);
+
 /* ---- w-product without a caller-supplied workspace ---------------------- */
 
 /* Size in bytes of the library-owned scratch array used by wp_wprod_noalloc. */

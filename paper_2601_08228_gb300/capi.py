@@ -69,6 +69,8 @@ _SIGNATURES = {
     "wp_wprod_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wprod": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _I, _P, _SZ, _P], _I),
     "wp_wprod_noalloc": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I, _I, _P], _I),
+    "wp_wprod_host_workspace": ([_I64, _I64, _I64, _I64, _I, _I, _I64, ctypes.POINTER(_SZ)], _I),
+    "wp_wprod_host": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _I64, _P, _SZ, _P], _I),
     "wp_wprod_backward_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_wprod_backward": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "wp_deblur_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
@@ -197,6 +199,41 @@ def wp_wprod(A, B, L, transA=False, transB=False, prec="fp32", out=None, ws=None
     C = torch.empty((p, n1, n4), dtype=torch.float32, device=A.device) if out is None else _req(out, "out")
     _check(lib().wp_wprod(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, int(transA), int(transB), pr,
                           _ptr(ws), ws.numel(), _stream()), "wp_wprod")
+    return C
+
+
+def _req_host(t, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != 3:
+        raise ValueError(f"{name} must be a contiguous host float32 tensor with 3 dims")
+    return t
+
+
+def wp_wprod_host_workspace(n1, n2, n4, p, L, prec, chunk_slices=0):
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_wprod_host_workspace(n1, n2, n4, p, L, _prec(prec), chunk_slices, ctypes.byref(nbytes)),
+           "wp_wprod_host_workspace")
+    return nbytes.value
+
+
+def wp_wprod_host(A, B, L, prec="fp32", out=None, ws=None, chunk_slices=0):
+    """C = A *w B for HOST tensors (pin them for overlap): chunks of whole
+    tube groups are copied in, multiplied and copied back on overlapping
+    streams.  Ordered on the current CUDA stream: C is complete once that
+    stream has been synchronised."""
+    _req_host(A, "A"), _req_host(B, "B")
+    p, n1, n2 = A.shape
+    if B.shape[0] != p or B.shape[1] != n2:
+        raise ValueError("shape mismatch in wp_wprod_host")
+    n4 = B.shape[2]
+    pr = _prec(prec)
+    need = wp_wprod_host_workspace(n1, n2, n4, p, L, pr, chunk_slices)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, torch.device("cuda", torch.cuda.current_device()))
+    C = torch.empty((p, n1, n4), dtype=torch.float32, pin_memory=A.is_pinned()) if out is None else _req_host(out, "out")
+    _check(lib().wp_wprod_host(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, pr, chunk_slices, _ptr(ws), ws.numel(),
+                               _stream()), "wp_wprod_host")
     return C
 
 

@@ -52,3 +52,12 @@ def test_host_validation_needs_no_gpu(libwprod):
     assert L.wp_wprod_workspace(4, 4, 4, 8, 3, 0, ctypes.byref(n)) == 0 and n.value > 0
     assert L.wp_wprod(fake, ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), 4, 4, 4, 8, 3, 0, 0, 0,
                       ctypes.c_void_p(4 << 20), 16, None) == 7           # workspace too small
+    # host-buffer w-product: chunks of whole tube groups, validated before any copy
+    assert L.wp_wprod_host_workspace(4, 4, 4, 16, 3, 0, 12, ctypes.byref(n)) == 2   # 12 % 2^3 != 0
+    assert L.wp_wprod_host_workspace(4, 4, 4, 12, 3, 0, 0, ctypes.byref(n)) == 3    # p % 2^L
+    assert L.wp_wprod_host_workspace(4, 4, 4, 16, 3, 0, 8, ctypes.byref(n)) == 0
+    two_chunks = n.value
+    assert L.wp_wprod_host_workspace(4, 4, 4, 16, 3, 0, 16, ctypes.byref(n)) == 0 and n.value > two_chunks
+    assert L.wp_wprod_host(None, fake, fake, 4, 4, 4, 16, 3, 0, 8, fake, 1 << 20, None) == 1
+    assert L.wp_wprod_host(fake, ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), 4, 4, 4, 16, 3, 0, 8,
+                           ctypes.c_void_p(4 << 20), 16, None) == 7           # workspace too small
