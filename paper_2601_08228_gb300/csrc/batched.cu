@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NW * 32) batched_jacobi_kernel(const BItem* __
     b.status = status;
     b.stats = stats;
     const float* A = it.Ah + int64_t(uk.y) * n1 * n2;
-    jblock::block_jacobi_slice<1, PPW, L::RPL, NW>(b, A, 0, vec, nullptr, smem_raw);
+    jblock::block_jacobi_slice<1, PPW, L::RPL, NW, false>(b, A, 0, vec, nullptr);
     // rebuild the rank-r slice from the original A_hat_k (still in global memory)
     float* Cr = it.Crh + int64_t(uk.y) * n1 * n2;
     if (!b.trans) {

@@ -196,11 +196,16 @@ struct PeerSum {
 // row-major), this CTA holds working rows [rank * rpc, (rank + 1) * rpc);
 // writes the leading r unit vectors to vo (m_len x r, row-major; any
 // memory space) and, from rank 0, the r singular values to so (if not
-// null).  smem_raw: block_smem<CL, PPW, RPL, NW>(a.n_pad) bytes.  Ends with a
-// cluster-wide barrier.
-template <int CL, int PPW, int RPL, int NW>
-__device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const float* A, int rank, float* vo,
-                                                   float* so, unsigned char* smem_raw) {
+// null).  GRID: the slice is a.slice0 + blockIdx.x / CL of a.X, the outputs
+// its rows of a.vec_out and a.sig_out (A, vo, so unused; the addresses are
+// formed where they are used, which keeps them out of the sweep loop's
+// registers).  Uses the first block_smem<CL, PPW, RPL, NW>(a.n_pad) bytes of
+// the kernel's dynamic shared memory.  Ends with a cluster-wide barrier.
+template <int CL, int PPW, int RPL, int NW, bool GRID>
+__device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const float* A_in, int rank_in,
+                                                   float* vo_in, float* so_in) {
+  // the kernel's dynamic shared memory, from offset 0
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   static_assert(PPW >= 2 && PPW <= 16 && (PPW & (PPW - 1)) == 0, "PPW: 2, 4, 8 or 16");
   static_assert(2 * PPW * RPL <= 64, "register budget: 2 PPW RPL <= 64 values per lane");
   constexpr int NTH = NW * 32;
@@ -220,6 +225,9 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
   int* rank_of = order + n_pad;                                     // [n_pad]
   float* mail = reinterpret_cast<float*>(smem_raw + block_mail_offset<CL, PPW, NW>(n_pad));
 
+  const int rank = GRID ? ((CL > 1) ? int(cg::this_cluster().block_rank()) : 0) : rank_in;
+  const int slice = GRID ? a.slice0 + int(blockIdx.x) / CL : 0;
+  const float* A = GRID ? a.X + int64_t(slice) * a.n1 * a.n2 : A_in;
   const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
   const int g = lane >> SHIFT, sub = lane & (LPP - 1);
   const bool active = warp < nw;
@@ -524,6 +532,7 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
     rank_of[c] = pos < a.r ? pos : -1;
   }
   __syncthreads();
+  float* vo = GRID ? a.vec_out + int64_t(slice) * a.m_len * a.r : vo_in;
   if (active) {
 #pragma unroll
     for (int j = 0; j < PPW; ++j) {
@@ -542,6 +551,7 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
       }
     }
   }
+  float* so = GRID ? a.sig_out + int64_t(slice) * a.r : so_in;
   if (rank == 0 && so)
     for (int kq = threadIdx.x; kq < a.r; kq += NTH) so[kq] = sqrtf(norms[order[kq]]);
   // no CTA may leave while a peer can still write into its shared memory
@@ -550,12 +560,7 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
 
 template <int CL, int PPW, int RPL>
 __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_block_kernel(JacobiArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int rank = (CL > 1) ? int(cg::this_cluster().block_rank()) : 0;
-  const int slice = a.slice0 + int(blockIdx.x) / CL;
-  block_jacobi_slice<CL, PPW, RPL, kBlockWarps>(a, a.X + int64_t(slice) * a.n1 * a.n2, rank,
-                                                a.vec_out + int64_t(slice) * a.m_len * a.r,
-                                                a.sig_out + int64_t(slice) * a.r, smem_raw);
+  block_jacobi_slice<CL, PPW, RPL, kBlockWarps, true>(a, nullptr, 0, nullptr, nullptr);
 }
 
 template <int CL, int PPW, int RPL>
