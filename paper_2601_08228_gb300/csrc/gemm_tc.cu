@@ -324,55 +324,74 @@ __global__ void __launch_bounds__(THREADS, 1)
 //                                registers (Eq. 3) and stores spatial C.  The
 //                                wavelet-domain product never reaches HBM.
 
+// One operand of lift_split_rows_kernel: spatial (p, R, C) in, Mallat-ordered
+// BF16 hi (/ lo) (p, R, Cp) out; `items` = (p / 2^L) * R * C / VEC.
+struct SplitOperand {
+  const float* in;
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  int R, C, Cp;
+  int64_t items;
+};
+
 template <int L, int VEC>
-__global__ void __launch_bounds__(256) lift_split_rows_kernel(const float* __restrict__ in,
-                                                              __nv_bfloat16* __restrict__ hi,
-                                                              __nv_bfloat16* __restrict__ lo, int64_t p, int R,
-                                                              int C, int Cp, int64_t total) {
+__device__ __forceinline__ void lift_split_item(const SplitOperand& d, int64_t p, int64_t item) {
   constexpr int G = 1 << L;
-  const int64_t plane = int64_t(R) * C;
+  const int64_t plane = int64_t(d.R) * d.C;
   const int64_t nvec = plane / VEC;
+  const int64_t g = item / nvec;
+  const int64_t e = (item - g * nvec) * VEC;
+  const int r = int(e / d.C), c = int(e - int64_t(r) * d.C);
+  float v[G][VEC];
+#pragma unroll
+  for (int t = 0; t < G; ++t) {
+    const float* src = d.in + (g * G + t) * plane + e;
+    if constexpr (VEC == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+      v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
+    } else {
+      v[t][0] = __ldg(src);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    float x[G], y[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) x[t] = v[t][j];
+    lift_group<L>(x, y);
+#pragma unroll
+    for (int t = 0; t < G; ++t) v[t][j] = y[t];
+  }
+#pragma unroll
+  for (int t = 0; t < G; ++t) {
+    const int64_t o = mallat_slice<L>(t, g, p) * int64_t(d.R) * d.Cp + int64_t(r) * d.Cp + c;
+    if constexpr (VEC == 4) {
+      __nv_bfloat16 h[4], l[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) split_bf16(v[t][jj], h[jj], l[jj]);
+      *reinterpret_cast<uint2*>(d.hi + o) = *reinterpret_cast<uint2*>(h);
+      if (d.lo) *reinterpret_cast<uint2*>(d.lo + o) = *reinterpret_cast<uint2*>(l);
+    } else {
+      __nv_bfloat16 h, l;
+      split_bf16(v[t][0], h, l);
+      d.hi[o] = h;
+      if (d.lo) d.lo[o] = l;
+    }
+  }
+}
+
+// Lift + BF16 split of one or two operands (d1.items = 0: one) in a single
+// grid-stride launch.  Every CTA signals at once that the dependent launch
+// (the GEMM, launched with programmatic serialisation) may start its
+// prologue; the GEMM waits for this grid's completion before reading.
+template <int L, int VEC>
+__global__ void __launch_bounds__(256) lift_split_rows_kernel(SplitOperand d0, SplitOperand d1, int64_t p) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int64_t total = d0.items + d1.items;
   for (int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; item < total;
        item += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t g = item / nvec;
-    const int64_t e = (item - g * nvec) * VEC;
-    const int r = int(e / C), c = int(e - int64_t(r) * C);
-    float v[G][VEC];
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const float* src = in + (g * G + t) * plane + e;
-      if constexpr (VEC == 4) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
-        v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
-      } else {
-        v[t][0] = __ldg(src);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < VEC; ++j) {
-      float x[G], y[G];
-#pragma unroll
-      for (int t = 0; t < G; ++t) x[t] = v[t][j];
-      lift_group<L>(x, y);
-#pragma unroll
-      for (int t = 0; t < G; ++t) v[t][j] = y[t];
-    }
-#pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const int64_t o = mallat_slice<L>(t, g, p) * int64_t(R) * Cp + int64_t(r) * Cp + c;
-      if constexpr (VEC == 4) {
-        __nv_bfloat16 h[4], l[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) split_bf16(v[t][j], h[j], l[j]);
-        *reinterpret_cast<uint2*>(hi + o) = *reinterpret_cast<uint2*>(h);
-        if (lo) *reinterpret_cast<uint2*>(lo + o) = *reinterpret_cast<uint2*>(l);
-      } else {
-        __nv_bfloat16 h, l;
-        split_bf16(v[t][0], h, l);
-        hi[o] = h;
-        if (lo) lo[o] = l;
-      }
-    }
+    if (item < d0.items) lift_split_item<L, VEC>(d0, p, item);
+    else lift_split_item<L, VEC>(d1, p, item - d0.items);
   }
 }
 
@@ -522,6 +541,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0 && lane == 0) {
     ptx::tma_prefetch_desc(&tmAh);
     ptx::tma_prefetch_desc(&tmBh);
+    // the operands are written by the preceding launch (programmatic
+    // serialisation): wait for its completion before the first load
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int issued = 0;
     for (int it = 0; it < iters && ok; ++it) {
       const int s = it % STAGES;
@@ -907,17 +929,30 @@ static int launch_lift_split_transpose(const float* B, __nv_bfloat16* hi, __nv_b
   return launch_status();
 }
 
+// Lift + split of A (and B, when given) into K- (resp. N-) contiguous BF16
+// hi/lo rows: one launch for both when both allow 16-byte accesses.
 template <int L>
 static int launch_lift_split_rows(const float* A, __nv_bfloat16* hi, __nv_bfloat16* lo, int64_t p, int R, int C,
-                                  int Cp, cudaStream_t st) {
-  const bool v4 = (C % 4 == 0) && aligned16(A);
-  const int64_t plane = int64_t(R) * C;
-  const int64_t total = (p >> L) * (v4 ? plane / 4 : plane);
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
-  WP_PROFILE("lift_split_bf16", st);
-  if (v4) lift_split_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(A, hi, lo, p, R, C, Cp, total);
-  else lift_split_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(A, hi, lo, p, R, C, Cp, total);
-  return launch_status();
+                                  int Cp, cudaStream_t st, const float* B = nullptr, __nv_bfloat16* bhi = nullptr,
+                                  __nv_bfloat16* blo = nullptr, int RB = 0, int CB = 0, int CBp = 0) {
+  auto operand = [&](const float* x, __nv_bfloat16* h, __nv_bfloat16* l, int r, int c, int cp, int vec) {
+    return SplitOperand{x, h, l, r, c, cp, (p >> L) * (int64_t(r) * c / vec)};
+  };
+  auto launch = [&](const SplitOperand& d0, const SplitOperand& d1, bool v4) -> int {
+    const int64_t total = d0.items + d1.items;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
+    WP_PROFILE("lift_split_bf16", st);
+    if (v4) lift_split_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(d0, d1, p);
+    else lift_split_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(d0, d1, p);
+    return launch_status();
+  };
+  const bool a4 = (C % 4 == 0) && aligned16(A);
+  const SplitOperand none{nullptr, nullptr, nullptr, 1, 1, 1, 0};
+  if (!B) return launch(operand(A, hi, lo, R, C, Cp, a4 ? 4 : 1), none, a4);
+  const bool b4 = (CB % 4 == 0) && aligned16(B);
+  if (a4 == b4) return launch(operand(A, hi, lo, R, C, Cp, a4 ? 4 : 1), operand(B, bhi, blo, RB, CB, CBp, a4 ? 4 : 1), a4);
+  WP_TRY(launch(operand(A, hi, lo, R, C, Cp, a4 ? 4 : 1), none, a4));
+  return launch(operand(B, bhi, blo, RB, CB, CBp, b4 ? 4 : 1), none, b4);
 }
 
 // One CTA per SM with all 512 TMEM columns (measured faster at L = 3 than
@@ -941,13 +976,17 @@ static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUte
   cfg.blockDim = dim3(tc::THREADS, 1, 1);
   cfg.dynamicSmemBytes = Lay::SMEM;
   cfg.stream = st;
-  cudaLaunchAttribute attrs[1];
+  cudaLaunchAttribute attrs[2];
   attrs[0].id = cudaLaunchAttributeClusterDimension;
   attrs[0].val.clusterDim.x = MC;
   attrs[0].val.clusterDim.y = 1;
   attrs[0].val.clusterDim.z = 1;
+  // programmatic serialisation: the prologue may overlap the operand
+  // preparation kernel; the kernel waits for it before its first load
+  attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attrs[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attrs;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   // output tensor map for the TMA-store epilogue: (p, M, N) FP32 with N % 4
   // == 0 (16-byte row stride), boxes of 32 columns x 128 rows x SPP slices
   constexpr int SPP = tc::fused_store_slices(Lay::G, Lay::BN, STAGES * Lay::STAGE);
@@ -976,9 +1015,9 @@ template <int L>
 static int fused_levels(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
                         bool x3, __nv_bfloat16* Ah, __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl,
                         int64_t Kp, float* Chat, cudaStream_t st) {
-  WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
   CUtensorMap mah, mal, mbh, mbl;
   if (Chat) {
+    WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
     // wide-tile GEMM into the wavelet-domain C_hat, then the inverse transform
     WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
     WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
@@ -1004,10 +1043,12 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
   if constexpr (BMN) {
     // W(B) in its natural layout (K rows of n4 columns), 64-column boxes
     const int64_t Np = pad8(n4);
-    WP_TRY(launch_lift_split_rows<L>(B, Bh, Bl, p, int(n2), int(n4), int(Np), st));
+    WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st, B, Bh, Bl, int(n2), int(n4),
+                                     int(Np)));
     WP_TRY(make_map(&mbh, Bh, n4, Np, n2, p, tc::BK));
     if (x3) WP_TRY(make_map(&mbl, Bl, n4, Np, n2, p, tc::BK));
   } else {
+    WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
     WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
     WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, BN));
     if (x3) WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, BN));
