@@ -162,15 +162,24 @@ constexpr int BM = 128;
 constexpr int BK = 64;          // BF16 elements per 128-byte swizzle row
 constexpr int THREADS = 192;
 
+// Persistent tcgen05 GEMM C[b] = op(A[b]) op(B[b]) over all (batch, row tile,
+// column tile) tiles of 128 x BN: one CTA per SM walks the tiles with stride
+// gridDim.x; the shared-memory stage ring runs on across tiles; two TMEM
+// accumulators (2 BN columns) let the epilogue of one tile overlap the MMAs
+// of the next.  Roles: warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues
+// the MMAs, warps 2..5 drain the accumulators (tcgen05.ld) and write C --
+// as 32 x 32 chunks staged in shared memory with the 128-byte swizzle and
+// stored by TMA (double-buffered per warp) when N % 4 == 0, else directly.
 template <int BN, int NPROD, int STAGES>
 struct Layout {
   static constexpr int NCOPY = (NPROD == 3) ? 2 : 1;   // BF16x3 keeps hi and lo copies
   static constexpr int A_TILE = BM * 128;               // 128-byte K rows (64 BF16 or 128 FP8)
   static constexpr int B_TILE = BN * 128;
   static constexpr int STAGE = NCOPY * (A_TILE + B_TILE);
-  static constexpr int BAR_OFF = STAGES * STAGE;
-  static constexpr int SMEM = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;   // + alignment slack
-  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr int STG_OFF = STAGES * STAGE;         // epilogue staging: 4 warps x 2 x 4 KB
+  static constexpr int BAR_OFF = STG_OFF + 4 * 2 * 4096;
+  static constexpr int SMEM = BAR_OFF + (2 * STAGES + 5) * 8 + 16 + 1024;   // + alignment slack
+  static constexpr uint32_t TMEM_COLS = (2 * BN) < 32 ? 32 : 2 * BN;
 };
 
 // NPROD: 1 = BF16, 3 = BF16x3, 8 = FP8 E4M3 (then sa_bits / sb_bits hold the
@@ -179,7 +188,8 @@ template <int BN, int NPROD, int STAGES>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                   float* __restrict__ C, int M, int N, int K, int* status, const unsigned* __restrict__ sa_bits,
+                   const __grid_constant__ CUtensorMap tmC, int tma_store, float* __restrict__ C, int M, int N,
+                   int K, int batch, int* status, const unsigned* __restrict__ sa_bits,
                    const unsigned* __restrict__ sb_bits) {
   using Lay = Layout<BN, NPROD, STAGES>;
   constexpr int BKE = (NPROD == 8) ? 128 : BK;          // K elements per 128-byte row
@@ -187,12 +197,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFF);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* tfull = empty + STAGES;     // [2] accumulator ready (MMA -> epilogue)
+  uint64_t* tempty = tfull + 2;         // [2] accumulator drained (epilogue -> MMA)
+  uint64_t* mma_done = tempty + 2;      // every issued MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
   const int nk = (K + BKE - 1) / BKE;
+  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const int64_t tiles = int64_t(batch) * mt * nt;
+  auto tile_of = [&](int64_t t, int& b, int& m0, int& n0) {
+    b = int(t / (int64_t(mt) * nt));
+    const int rem = int(t - int64_t(b) * mt * nt);
+    m0 = (rem / nt) * BM;
+    n0 = (rem % nt) * BN;
+  };
 
   auto a_tile = [&](int s, int copy) { return smem + s * Lay::STAGE + copy * Lay::A_TILE; };
   auto b_tile = [&](int s, int copy) {
@@ -204,7 +223,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::mbar_init(&full[s], 1);
       ptx::mbar_init(&empty[s], 1);
     }
-    ptx::mbar_init(accum, 1);
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&tfull[a], 1);
+      ptx::mbar_init(&tempty[a], 4);
+    }
+    ptx::mbar_init(mma_done, 1);
     ptx::fence_mbar_init();
   }
   if (warp == 1) ptx::tmem_alloc(tmem_slot, Lay::TMEM_COLS);
@@ -218,88 +241,126 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---- TMA producer ----
     ptx::tma_prefetch_desc(&tmAh);
     ptx::tma_prefetch_desc(&tmBh);
-    int issued = 0;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES) ok = ptx::mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, status);
-      if (!ok) break;
-      ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
-      ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BKE, m0, b, &full[s]);
-      if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BKE, m0, b, &full[s]);
-      ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BKE, n0, b, &full[s]);
-      if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BKE, n0, b, &full[s]);
-      ++issued;
+    // operands written by the preceding launch (programmatic serialisation)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    uint32_t it = 0;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      int b, m0, n0;
+      tile_of(t, b, m0, n0);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const uint32_t s = it % STAGES;
+        if (it >= uint32_t(STAGES)) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
+        if (!ok) break;
+        ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
+        ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BKE, m0, b, &full[s]);
+        if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BKE, m0, b, &full[s]);
+        ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BKE, n0, b, &full[s]);
+        if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BKE, n0, b, &full[s]);
+      }
     }
     if (!ok) {
-      // drain: wait (bounded) for the loads still in flight into this CTA's ring
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        ptx::mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, nullptr, 100000000ull);
+      // drain: wait (bounded) for the loads still in flight into the ring
+      for (uint32_t k = (it > uint32_t(STAGES) ? it - STAGES : 0); k < it; ++k)
+        ptx::mbar_wait(&full[k % STAGES], (k / STAGES) & 1, nullptr, 100000000ull);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     constexpr uint32_t idesc = (NPROD == 8) ? ptx::idesc_e4m3_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % STAGES;
-      ok = ptx::mbar_wait(&full[s], (kb / STAGES) & 1, status);
+    uint32_t it = 0, ti = 0;
+    for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
+      const uint32_t acc = ti & 1;
+      // the epilogue has drained this accumulator (both start free)
+      ok = ptx::mbar_wait(&tempty[acc], ((ti >> 1) & 1) ^ 1, status);
       if (!ok) break;
       ptx::tc_fence_after();
+      const uint32_t d = tmem + acc * BN;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const uint32_t s = it % STAGES;
+        ok = ptx::mbar_wait(&full[s], (it / STAGES) & 1, status);
+        if (!ok) break;
+        ptx::tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {            // 4 MMAs of 32 bytes of K per 128-byte row
-        const uint64_t ah = ptx::sdesc_kmajor_sw128(a_tile(s, 0) + kk * 32);
-        const uint64_t bh = ptx::sdesc_kmajor_sw128(b_tile(s, 0) + kk * 32);
-        if (NPROD == 8) {
-          ptx::mma_e4m3(tmem, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-          continue;
+        for (int kk = 0; kk < 4; ++kk) {            // 4 MMAs of 32 bytes of K per 128-byte row
+          const uint64_t ah = ptx::sdesc_kmajor_sw128(a_tile(s, 0) + kk * 32);
+          const uint64_t bh = ptx::sdesc_kmajor_sw128(b_tile(s, 0) + kk * 32);
+          if (NPROD == 8) {
+            ptx::mma_e4m3(d, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            continue;
+          }
+          ptx::mma_bf16(d, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          if (NPROD == 3) {
+            const uint64_t al = ptx::sdesc_kmajor_sw128(a_tile(s, 1) + kk * 32);
+            const uint64_t bl = ptx::sdesc_kmajor_sw128(b_tile(s, 1) + kk * 32);
+            ptx::mma_bf16(d, ah, bl, idesc, 1u);
+            ptx::mma_bf16(d, al, bh, idesc, 1u);
+          }
         }
-        ptx::mma_bf16(tmem, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-        if (NPROD == 3) {
-          const uint64_t al = ptx::sdesc_kmajor_sw128(a_tile(s, 1) + kk * 32);
-          const uint64_t bl = ptx::sdesc_kmajor_sw128(b_tile(s, 1) + kk * 32);
-          ptx::mma_bf16(tmem, ah, bl, idesc, 1u);
-          ptx::mma_bf16(tmem, al, bh, idesc, 1u);
-        }
+        ptx::mma_commit(&empty[s]);
       }
-      ptx::mma_commit(&empty[s]);
+      if (!ok) break;
+      ptx::mma_commit(&tfull[acc]);
     }
-    ptx::mma_commit(accum);   // also on failure: tracks completion of all issued MMAs
+    ptx::mma_commit(mma_done);   // also on failure: tracks completion of all issued MMAs
   } else if (warp >= 2) {
     // ---- epilogue ----
-    ok = ptx::mbar_wait(accum, 0, status);
-    ptx::tc_fence_after();
-    if (ok) {
-      const int quad = warp & 3;               // TMEM lanes this warp may access
-      const int row = m0 + quad * 32 + lane;
-      float* crow = C + (int64_t(b) * M + row) * N;
-      const bool vec = (N % 4) == 0;
+    const int quad = warp & 3;                  // TMEM lanes this warp may access
+    const int ew = warp - 2;                    // staging buffers of this warp
+    uint32_t ti = 0, chunk = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
+      const uint32_t acc = ti & 1;
+      if (ok) ok = ptx::mbar_wait(&tfull[acc], (ti >> 1) & 1, status);
+      if (!ok) break;
+      ptx::tc_fence_after();
+      int b, m0, n0;
+      tile_of(t, b, m0, n0);
       float scale = 1.f;
       if constexpr (NPROD == 8) scale = fp8_scale(sa_bits[b]) * fp8_scale(sb_bits[b]);
+      const int row = m0 + quad * 32 + lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= N) break;
         float v[32];
-        ptx::tmem_ld_32cols(tmem + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
+        ptx::tmem_ld_32cols(tmem + (uint32_t(quad * 32) << 16) + acc * BN + uint32_t(c0), v);
         if constexpr (NPROD == 8) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] *= scale;
         }
-        if (row < M) {
-          const int col = n0 + c0;
-          if (vec && col + 32 <= N) {
+        if (tma_store) {
+          uint8_t* stg = smem + Lay::STG_OFF + (ew * 2 + (chunk & 1)) * 4096;
+          // the store issued from this buffer two chunks ago has read it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(crow + col + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-          } else {
-            for (int j = 0; j < 32 && col + j < N; ++j) crow[col + j] = v[j];
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<float4*>(stg + lane * 128 + ((q ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            ptx::tma_store_3d(&tmC, stg, n0 + c0, m0 + quad * 32, b);
+            ptx::bulk_commit();
           }
+          ++chunk;
+        } else if (row < M) {
+          float* crow = C + (int64_t(b) * M + row) * N;
+          const int col = n0 + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col + j < N) crow[col + j] = v[j];
         }
       }
+      // this warp's reads of the accumulator are complete
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
     }
+    if (lane == 0) ptx::bulk_wait_all();
   }
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     ptx::tc_fence_after();
-    if (!ok) ptx::mbar_wait(accum, 0, nullptr, 100000000ull);   // MMAs finished before TMEM is freed
+    ptx::mbar_wait(mma_done, 0, nullptr, 100000000ull);   // MMAs finished before TMEM is freed
     __syncwarp();
     ptx::tmem_dealloc(tmem, Lay::TMEM_COLS);
   }
@@ -810,16 +871,33 @@ static int launch_gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUten
                        float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st, const char* name,
                        const unsigned* sa = nullptr, const unsigned* sb = nullptr) {
   using Lay = tc::Layout<BN, NPROD, STAGES>;
+  auto kern = tc::tc_gemm_kernel<BN, NPROD, STAGES>;
   static bool attr = false;
   if (!attr) {
-    WP_CUDA_TRY(cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, NPROD, STAGES>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
+    WP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
     attr = true;
   }
-  const dim3 grid{unsigned((N + BN - 1) / BN), unsigned((M + tc::BM - 1) / tc::BM), unsigned(p)};
+  // C as (p, M, N) FP32, 32 x 32 boxes for the TMA-store epilogue (N % 4 == 0)
+  CUtensorMap mc = ah;
+  int tma_store = 0;
+  if (N % 4 == 0 && aligned16(C)) {
+    WP_TRY(make_map_f32(&mc, C, N, M, p, 32, 32, 1));
+    tma_store = 1;
+  }
+  const int64_t tiles = p * ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(std::min<int64_t>(tiles, sm_count())), 1, 1);
+  cfg.blockDim = dim3(tc::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Lay::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attrs[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
   WP_PROFILE(name, st);
-  tc::tc_gemm_kernel<BN, NPROD, STAGES><<<grid, tc::THREADS, Lay::SMEM, st>>>(ah, al, bh, bl, C, int(M), int(N),
-                                                                              int(K), device_status_ptr(), sa, sb);
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, mc, tma_store, C, int(M), int(N), int(K), int(p),
+                                 device_status_ptr(), sa, sb));
   return launch_status();
 }
 
