@@ -183,8 +183,9 @@ struct Layout {
 };
 
 // NPROD: 1 = BF16, 3 = BF16x3, 8 = FP8 E4M3 (then sa_bits / sb_bits hold the
-// per-slice amax of each operand and the epilogue applies s_a s_b).
-template <int BN, int NPROD, int STAGES>
+// per-slice amax of each operand and the epilogue applies s_a s_b).  BMN: B
+// is MN-major (N contiguous, 64-column boxes; BF16 only).
+template <int BN, int NPROD, int STAGES, bool BMN = false>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                    const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                    int K, int batch, int* status, const unsigned* __restrict__ sa_bits,
                    const unsigned* __restrict__ sb_bits) {
   using Lay = Layout<BN, NPROD, STAGES>;
+  static_assert(!BMN || (NPROD != 8 && BN % 64 == 0), "MN-major B: BF16, 64-column blocks");
   constexpr int BKE = (NPROD == 8) ? 128 : BK;          // K elements per 128-byte row
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -254,8 +256,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
         ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BKE, m0, b, &full[s]);
         if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BKE, m0, b, &full[s]);
-        ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BKE, n0, b, &full[s]);
-        if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BKE, n0, b, &full[s]);
+        if constexpr (BMN) {
+#pragma unroll
+          for (int j = 0; j < BN / 64; ++j) {
+            ptx::tma_load_3d(b_tile(s, 0) + j * 8192, &tmBh, n0 + 64 * j, kb * BK, b, &full[s]);
+            if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1) + j * 8192, &tmBl, n0 + 64 * j, kb * BK, b, &full[s]);
+          }
+        } else {
+          ptx::tma_load_3d(b_tile(s, 0), &tmBh, kb * BKE, n0, b, &full[s]);
+          if (NPROD == 3) ptx::tma_load_3d(b_tile(s, 1), &tmBl, kb * BKE, n0, b, &full[s]);
+        }
       }
     }
     if (!ok) {
@@ -265,7 +275,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    constexpr uint32_t idesc = (NPROD == 8) ? ptx::idesc_e4m3_f32(BM, BN) : ptx::idesc_bf16_f32(BM, BN);
+    constexpr uint32_t idesc = (NPROD == 8)  ? ptx::idesc_e4m3_f32(BM, BN)
+                               : BMN         ? ptx::idesc_bf16_f32_bmn(BM, BN)
+                                             : ptx::idesc_bf16_f32(BM, BN);
+    auto bdesc = [&](int s, int copy, int kk) {
+      if constexpr (BMN) return ptx::sdesc_mnmajor_sw128(b_tile(s, copy) + kk * 2048, 8192);
+      else return ptx::sdesc_kmajor_sw128(b_tile(s, copy) + kk * 32);
+    };
     uint32_t it = 0, ti = 0;
     for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++ti) {
       const uint32_t acc = ti & 1;
@@ -282,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {            // 4 MMAs of 32 bytes of K per 128-byte row
           const uint64_t ah = ptx::sdesc_kmajor_sw128(a_tile(s, 0) + kk * 32);
-          const uint64_t bh = ptx::sdesc_kmajor_sw128(b_tile(s, 0) + kk * 32);
+          const uint64_t bh = bdesc(s, 0, kk);
           if (NPROD == 8) {
             ptx::mma_e4m3(d, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
             continue;
@@ -290,7 +306,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ptx::mma_bf16(d, ah, bh, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
           if (NPROD == 3) {
             const uint64_t al = ptx::sdesc_kmajor_sw128(a_tile(s, 1) + kk * 32);
-            const uint64_t bl = ptx::sdesc_kmajor_sw128(b_tile(s, 1) + kk * 32);
+            const uint64_t bl = bdesc(s, 1, kk);
             ptx::mma_bf16(d, ah, bl, idesc, 1u);
             ptx::mma_bf16(d, al, bh, idesc, 1u);
           }
@@ -866,12 +882,12 @@ static int split_operand(const float* X, int64_t rows, int64_t K, int64_t Kp, in
   return launch_status();
 }
 
-template <int BN, int NPROD, int STAGES>
+template <int BN, int NPROD, int STAGES, bool BMN = false>
 static int launch_gemm(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                        float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st, const char* name,
                        const unsigned* sa = nullptr, const unsigned* sb = nullptr) {
   using Lay = tc::Layout<BN, NPROD, STAGES>;
-  auto kern = tc::tc_gemm_kernel<BN, NPROD, STAGES>;
+  auto kern = tc::tc_gemm_kernel<BN, NPROD, STAGES, BMN>;
   static bool attr = false;
   if (!attr) {
     WP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
@@ -1095,18 +1111,20 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
                         int64_t Kp, float* Chat, cudaStream_t st) {
   CUtensorMap mah, mal, mbh, mbl;
   if (Chat) {
-    WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st));
-    // wide-tile GEMM into the wavelet-domain C_hat, then the inverse transform
-    WP_TRY(launch_lift_split_transpose<L>(B, Bh, Bl, p, int(n2), int(n4), int(Kp), st));
+    // lift + split of A and of B (B in its natural layout, MN-major for the
+    // MMA) in one launch, the persistent wide-tile GEMM into the
+    // wavelet-domain C_hat, then the inverse transform
+    const int64_t Np = pad8(n4);
+    WP_TRY(launch_lift_split_rows<L>(A, Ah, Al, p, int(n1), int(n2), int(Kp), st, B, Bh, Bl, int(n2), int(n4),
+                                     int(Np)));
     WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
+    WP_TRY(make_map(&mbh, Bh, n4, Np, n2, p, tc::BK));
     if (x3) {
       WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, tc::BM));
-      WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, 128));
-      WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, 128));
-      WP_TRY((launch_gemm<128, 3, 3>(mah, mal, mbh, mbl, Chat, n1, n4, n2, p, st, "tc_gemm_bf16x3")));
+      WP_TRY(make_map(&mbl, Bl, n4, Np, n2, p, tc::BK));
+      WP_TRY((launch_gemm<128, 3, 3, true>(mah, mal, mbh, mbl, Chat, n1, n4, n2, p, st, "tc_gemm_bf16x3")));
     } else {
-      WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, 256));
-      WP_TRY((launch_gemm<256, 1, 4>(mah, mah, mbh, mbh, Chat, n1, n4, n2, p, st, "tc_gemm_bf16")));
+      WP_TRY((launch_gemm<256, 1, 4, true>(mah, mah, mbh, mbh, Chat, n1, n4, n2, p, st, "tc_gemm_bf16")));
     }
     return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st);
   }
@@ -1147,10 +1165,16 @@ int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t
   const int64_t Kp = pad8(n2);
   const bool x3 = (prec == WP_PREC_BF16X3);
   // The inverse-lift epilogue needs all 2^L accumulators of a tile in TMEM,
-  // so its tile is only 512 / 2^L wide; when that would re-read A more than
-  // four times, keep the wide-tile GEMM and inverse-lift in a separate pass.
+  // so its tile is only 512 / 2^L wide.  Measured on GB300 (BF16x3, the
+  // 256 x 256 x 192 L = 3 case and neighbours): the fused kernel wins with
+  // wide tiles (L <= 2), short K (n2 <= 64, where the wavelet-domain round
+  // trip of C dominates) and small slices (n1, n4 <= 128); otherwise the
+  // persistent wide-tile GEMM into C_hat plus a separate inverse lift is
+  // faster (88 vs 96 us at 256 x 256 x 192), and it is the only choice when
+  // the fused tile would re-read A more than four times.
   const int64_t bn_fused = 512 >> L;
-  const bool epilogue_fused = (n4 + bn_fused - 1) / bn_fused <= 4;
+  const bool epilogue_fused = (n4 + bn_fused - 1) / bn_fused <= 4 &&
+                              (L <= 2 || n2 <= 64 || (n1 <= 128 && n4 <= 128));
   Carver cv(ws, ws_bytes);
   float* Chat = epilogue_fused ? nullptr : cv.take<float>(size_t(p) * n1 * n4);
   // B operand: (p, n2, pad8(n4)) MN-major on the fused-epilogue path at

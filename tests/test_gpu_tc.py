@@ -126,7 +126,8 @@ FUSED_CASES = [
     (64, 50, 96, 21, 5),        # BN = 16, two groups
     (16, 1, 1, 1, 4),           # degenerate
     (32, 64, 64, 300, 4),       # wide output: the wide-tile GEMM + separate inverse lift
-    (16, 96, 72, 256, 3),       # 4 N tiles: A multicast over a 4-CTA cluster, MN-major B
+    (16, 96, 72, 256, 3),       # wide-tile persistent GEMM (MN-major B) + separate inverse lift
+    (16, 96, 48, 256, 3),       # short K: fused, 4 N tiles, A multicast over a 4-CTA cluster
     (8, 160, 64, 200, 2),       # 2 ragged N tiles of 128: 2-CTA cluster, MN-major B in two 64-column blocks
     (4, 300, 128, 512, 1),      # BN = 256 (four 64-column B blocks), 3 M tiles, 2-CTA cluster
 ]
