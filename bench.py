@@ -54,7 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
-    ap.add_argument("--profile-case", choices=["lift", "gemm", "wprod", "jacobi", "batched"], default=None,
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "wprod", "jacobi", "batched"],
+                    default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
 
@@ -577,6 +578,12 @@ def run_profile_case(case):
         A = torch.rand((192, 256, 256), device="cuda")
         B = torch.rand((192, 256, 256), device="cuda")
         capi.wp_facewise(A, B, prec="bf16x3")
+    elif case == "gemm_large":
+        # the precision study's face-product shape (1024 x 1024 by 1024 x 512), 64 slices: 1.1 GB
+        A = torch.rand((64, 1024, 1024), device="cuda")
+        B = torch.rand((64, 1024, 512), device="cuda")
+        for prec in ("bf16", "bf16x3"):
+            capi.wp_facewise(A, B, prec=prec)
     elif case == "wprod":
         A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
         capi.wp_wprod(A, B, WORKLOAD["L"], prec="bf16x3")
