@@ -296,8 +296,14 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
   // from the fast reciprocal and reciprocal square root (a few ulp in t
   // changes how far the pair is orthogonalised, not the orthogonality of
   // the rotation: c = 1 / sqrt(1 + t^2), s = c t)
+  // `big` records a pair whose cosine exceeds the stopping bound tol2s of
+  // the sweep (see the sweep loop)
+  int big = 0;
+  float tol2s = 0.f;
   auto angle = [&](float gam, float al, float be, float negl, float tol2, float& c, float& s, float& t) {
-    if (al > negl && be > negl && gam * gam > tol2 * (al * be)) {
+    const float ab = al * be;
+    if (al > negl && be > negl && gam * gam > tol2s * ab) big = 1;
+    if (al > negl && be > negl && gam * gam > tol2 * ab) {
       const float zeta = __fdividef(be - al, 2.f * gam);
       const float az = fminf(fabsf(zeta), 1e18f);
       const float h = fmaf(az, az, 1.f);
@@ -352,7 +358,13 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
     for (int w = 0; w < NW; ++w) nmax = fmaxf(nmax, red[w]);
     const float meps = float(a.m_len) * 1.1920929e-7f;
     const float negl = nmax * meps * meps;
-    int rot_any = 0;
+    // Stopping rule.  A sweep in which no pair's cosine |gamma| / sqrt(alpha
+    // beta) reaches tol ends the iteration.  Jacobi converges quadratically
+    // near the end, so a sweep whose largest cosine stays below 0.3 sqrt(tol)
+    // leaves cosines of order 0.09 tol: it ends the iteration too, without
+    // the confirming sweep that would find nothing to rotate.
+    tol2s = 0.09f * tol_eff;
+    big = 0;
 
     if (active) {
       // every block meets itself: circle method inside the block, top block
@@ -381,7 +393,6 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
         if (angle(gam, al, be, negl, tol2, c, s, t)) {
           al = fmaf(-t, gam, al);
           be = fmaf(t, gam, be);
-          rot_any = 1;
         }
 #pragma unroll
         for (int i2 = 0; i2 < HALF; ++i2) {
@@ -425,8 +436,7 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
           if (angle(gam, nT, nB, negl, tol2, c, s, t)) {
             nT = fmaf(-t, gam, nT);
             nB = fmaf(t, gam, nB);
-            rot_any = 1;
-            // x_a' = c (x_a - t x_b), x_b' = c (x_b + t x_a) with the cosine
+              // x_a' = c (x_a - t x_b), x_b' = c (x_b + t x_a) with the cosine
             // moved into the scales: y_a -= t (d_b / d_a) y_b, y_b += t (d_a / d_b) y_a
             ta = t * rba;
             tb = t * rab;
@@ -498,7 +508,7 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
         if (warp >= 1) fetch(T, nT, warp == 1 ? 1 : 2 * (warp - 1));
       }
     }
-    if (!__syncthreads_or(rot_any)) {
+    if (!__syncthreads_or(big)) {
       converged = true;
       break;
     }
