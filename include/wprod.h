@@ -164,11 +164,12 @@ WP_API int wp_wprod(const float* A, const float* B, float* C, int64_t n1, int64_
  * copied back, on three library-owned streams that start after the work
  * already queued on `stream`; `stream` then waits for the last copy back.
  * The result equals wp_wprod's on the same slices.  chunk_slices = 0 picks
- * about p / 4 (rounded up to a multiple of 2^L).
+ * one tube group for the first and the last chunk (a short copy before the
+ * first product and after the last) and about p / 4 slices for the others.
  *   - Page-locked host buffers let the copies overlap; pageable ones work
  *     but each copy then blocks the host.
- *   - ws: device memory of wp_wprod_host_workspace() bytes (two chunks of A,
- *     B and C, and one chunk's wp_wprod workspace), 256-byte aligned.
+ *   - ws: device memory of wp_wprod_host_workspace() bytes (three chunks of
+ *     A, B and C, and one chunk's wp_wprod workspace), 256-byte aligned.
  *   - All calls on one device share the three streams and their events:
  *     calls from several host threads on one device must be serialised.
  * Errors: as wp_wprod (shapes, levels, precision, workspace), WP_ERR_NULL
