@@ -105,3 +105,27 @@ def test_batched_4096_items_sampled():
     idx = np.random.default_rng(0).choice(4096, 24, replace=False)
     _check_items(items, dev, idx, 8)
     assert capi.wp_get_device_error() == 0
+
+
+def test_batched_small_and_degenerate_items():
+    """Items narrower than one 8-column block pair (n1, n2 in 1..20, padded
+    with zero columns in the Jacobi phase), L = 0..2, ranks up to min(n1, n2),
+    every item against the oracle."""
+    rng = np.random.default_rng(7)
+    items = []
+    for _ in range(40):
+        n1, n2, n4 = (int(x) for x in rng.integers(1, 21, size=3))
+        L = int(rng.integers(0, 3))
+        p = (1 << L) * int(rng.integers(1, 4))
+        items.append(dict(n1=n1, n2=n2, n4=n4, p=p, L=L,
+                          A=rng.uniform(-1, 1, (p, n1, n2)).astype(np.float32),
+                          B=rng.uniform(-1, 1, (p, n2, n4)).astype(np.float32)))
+    dev = _device_items(items, 1)
+    for d, it in zip(dev, items):
+        d["r"] = int(rng.integers(1, min(it["n1"], it["n2"]) + 1))
+    bl = capi.BatchedLaunch(dev)
+    bl.run()
+    for h, d in zip(items, dev):
+        assert O.rel_fro(host(d["C"]), O.wprod(h["A"], h["B"], h["L"])) <= 1e-5
+        assert O.rel_fro(host(d["C_r"]), O.wsvd(h["A"], h["L"], d["r"])) <= _rec_tol(h["A"], h["L"], d["r"])
+    assert capi.wp_get_device_error() == 0

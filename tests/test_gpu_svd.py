@@ -52,6 +52,7 @@ SVD_CASES = [
     (6, 1, 5, 1, 1),         # single-row slices
     (4, 150, 130, 2, 10),    # cluster path
     (2, 256, 256, 1, 20),
+    (2, 320, 300, 1, 10),    # more than 256 columns: 16-column blocks, 8-CTA cluster
 ]
 
 
