@@ -246,7 +246,12 @@ WP_API int wp_deblur_step(const float* K, const float* Y, float* X, int64_t n1, 
  * -- singular vectors as columns, singular values in descending order.  With
  * factors_in_wavelet_domain = 1 they are the per-slice factors in Mallat
  * order; with 0 they are mapped to the spatial domain with W^{-1} (Thm 2.5).
- * Singular vectors are determined up to sign. */
+ * Singular vectors are determined up to sign.
+ * Size limit: a slice's working matrix (max(n1, n2) rows, min(n1, n2)
+ * columns) must fit on one 8-CTA thread-block cluster -- in shared memory
+ * (about n_cols * rows / 8 <= 51200 floats, e.g. 640 x 640) or in registers
+ * (up to 512 columns and 8 x 64 rows); other shapes return
+ * WP_ERR_UNSUPPORTED (the same limit holds for wp_wpinv). */
 WP_API int wp_wsvd_workspace(int64_t n1, int64_t n2, int64_t p, int L, int r, size_t* bytes);
 WP_API int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V, int64_t n1, int64_t n2,
             int64_t p, int L, int r, int sparse, int factors_in_wavelet_domain, void* ws,
