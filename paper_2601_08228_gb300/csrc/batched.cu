@@ -136,11 +136,14 @@ template <int PPW, int NW>
 struct BJ {
   static constexpr int RPL = 2;
   static constexpr size_t BLOCK = jblock::block_smem<1, PPW, RPL, NW>(BMAX);   // n_pad <= 64
-  static constexpr size_t SMEM = BLOCK + size_t(BMAX) * BMAX * sizeof(float);  // + leading vectors
+  // + the leading vectors, max(n1, n2) x r floats (at most 64 x 64)
+  static size_t smem(int vec_floats) { return BLOCK + (size_t(vec_floats) * sizeof(float) + 15) / 16 * 16; }
 };
 
+// 64 registers: 1024 threads per SM's worth of CTAs (8 of 4 warps, 4 of 8)
+// when shared memory allows.
 template <int PPW, int NW>
-__global__ void __launch_bounds__(NW * 32) batched_jacobi_kernel(const BItem* __restrict__ items,
+__global__ void __launch_bounds__(NW * 32, 32 / NW) batched_jacobi_kernel(const BItem* __restrict__ items,
                                                                  const int2* __restrict__ units, int64_t nunits,
                                                                  int max_sweeps, int* status,
                                                                  unsigned long long* stats) {
@@ -289,27 +292,31 @@ static int launch_batched_gemm(const BItem* items, const int2* units, int64_t n,
 }
 
 template <int PPW, int NW>
-static int launch_batched_jacobi_t(const BItem* items, const int2* units, int64_t n, cudaStream_t st) {
+static int launch_batched_jacobi_t(const BItem* items, const int2* units, int64_t n, int vec_floats,
+                                   cudaStream_t st) {
   using L = BJ<PPW, NW>;
-  static int per_sm = 0;
-  if (!per_sm) {
+  const size_t smem = L::smem(vec_floats);
+  static bool attr = false;
+  if (!attr) {
     WP_CUDA_TRY(cudaFuncSetAttribute(batched_jacobi_kernel<PPW, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(L::SMEM)));
-    WP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_jacobi_kernel<PPW, NW>, NW * 32,
-                                                              L::SMEM));
-    if (per_sm < 1) per_sm = 1;
+                                     int(L::smem(BMAX * BMAX))));
+    attr = true;
   }
+  int per_sm = 0;
+  WP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_jacobi_kernel<PPW, NW>, NW * 32, smem));
+  if (per_sm < 1) per_sm = 1;
   const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * per_sm);
   WP_PROFILE("batched_jacobi", st);
-  batched_jacobi_kernel<PPW, NW><<<unsigned(std::max<int64_t>(grid, 1)), NW * 32, L::SMEM, st>>>(
+  batched_jacobi_kernel<PPW, NW><<<unsigned(std::max<int64_t>(grid, 1)), NW * 32, smem, st>>>(
       items, units, n, 40, device_status_ptr(), jacobi_stats_ptr());
   return launch_status();
 }
 
 // threads: 128 (4 warps, blocks of 8 columns) or 256 (8 warps, blocks of 4)
-static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t n, int threads, cudaStream_t st) {
-  if (threads == 256) return launch_batched_jacobi_t<4, 8>(items, units, n, st);
-  return launch_batched_jacobi_t<8, 4>(items, units, n, st);
+static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t n, int threads, int vec_floats,
+                                 cudaStream_t st) {
+  if (threads == 256) return launch_batched_jacobi_t<4, 8>(items, units, n, vec_floats, st);
+  return launch_batched_jacobi_t<8, 4>(items, units, n, vec_floats, st);
 }
 
 // Time one candidate configuration of a phase (median of 3 runs).
@@ -396,6 +403,9 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
   plan->n_units = lay.nunits;
   plan->gemm_threads = 256;
   plan->svd_threads = 128;
+  plan->svd_vec_floats = 1;
+  for (int i = 0; i < count; ++i)
+    plan->svd_vec_floats = std::max(plan->svd_vec_floats, std::max(items[i].n1, items[i].n2) * items[i].r);
   if (tune) {
     // autotune the CTA sizes of the face-product and Jacobi phases on the
     // planned work (phase 1 first so that the operands are real)
@@ -409,7 +419,8 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
     }
     best = 1e30f;
     for (int thr : {128, 256}) {
-      const float t = time_candidate([&] { launch_batched_jacobi(di, du, lay.nunits, thr, st); }, st);
+      const float t =
+          time_candidate([&] { launch_batched_jacobi(di, du, lay.nunits, thr, plan->svd_vec_floats, st); }, st);
       if (t < best) { best = t; plan->svd_threads = thr; }
     }
     WP_CUDA_TRY(cudaGetLastError());
@@ -420,6 +431,7 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
 extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream) {
   if (!plan || !ws) return WP_ERR_NULL;
   if (plan->count < 1 || plan->n_units < 1) return WP_ERR_SHAPE;
+  if (plan->svd_vec_floats < 1 || plan->svd_vec_floats > BMAX * BMAX) return WP_ERR_SHAPE;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = as_stream(stream);
   const BItem* di = reinterpret_cast<const BItem*>(base + plan->items_off);
@@ -427,7 +439,7 @@ extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream)
   WP_TRY(launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_fwd_off), plan->n_lift_fwd,
                              plan->lift_fwd_blocks, st));
   WP_TRY(launch_batched_gemm(di, du, plan->n_units, plan->gemm_threads, st));
-  WP_TRY(launch_batched_jacobi(di, du, plan->n_units, plan->svd_threads, st));
+  WP_TRY(launch_batched_jacobi(di, du, plan->n_units, plan->svd_threads, plan->svd_vec_floats, st));
   return launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_inv_off), plan->n_lift_inv,
                              plan->lift_inv_blocks, st);
 }
