@@ -205,6 +205,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // every CTA is resident from the start (one per SM): the next kernel of the
+  // stream, if launched with programmatic serialisation, may be scheduled now
+  // (it waits for this grid's completion before reading)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int nk = (K + BKE - 1) / BKE;
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
   const int64_t tiles = int64_t(batch) * mt * nt;

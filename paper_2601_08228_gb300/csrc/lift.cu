@@ -66,11 +66,16 @@ __device__ __forceinline__ void store_vec(float* p, const float* v) {
 }
 
 // Register kernel: grid-stride over items = (group g, vector index e).
+// Launched with programmatic serialisation: it may start while the previous
+// kernel of the stream finishes and waits for that kernel's completion before
+// reading; it lets its own successor start early the same way.
 template <int L, int VEC, int OP>
 __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__ in,
                                                        float* __restrict__ out, int64_t plane,
                                                        int64_t p, int64_t nvec, int64_t total) {
   constexpr int G = 1 << L;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; item < total;
        item += int64_t(gridDim.x) * blockDim.x) {
     const int64_t g = item / nvec;
@@ -184,8 +189,17 @@ static int launch_reg(const float* in, float* out, int64_t plane, int64_t p, cud
   const int64_t cap = int64_t(sm_count()) * 8;   // 2048 resident threads per SM
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(blocks), 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   WP_PROFILE(kLiftNames[OP], st);
-  lift_reg_kernel<L, VEC, OP><<<unsigned(blocks), threads, 0, st>>>(in, out, plane, p, nvec, total);
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP>, in, out, plane, p, nvec, total));
   return launch_status();
 }
 
