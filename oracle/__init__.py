@@ -24,9 +24,11 @@ Modules:
   grad       gradient of <G, A *w B> with respect to A and B (adjoint route)
   deblur     gradient-descent deblurring objective ||K *w X - Y||^2 + lam||X||^2
   metrics    relative Frobenius error, PSNR (Sec. IV-A)
+  quant      emulation of the FP8 (E4M3, one scale per slice) face-product
 
 Pinned by tests/test_oracle_*.py against the paper's worked examples
-(Example 2.2, Remark 2.2), closed forms and invariants.  Nothing here is
+(Example 2.2, Remark 2.2), closed forms and invariants; the E4M3 rounding of
+`quant` against the format's own value table and PyTorch's float8_e4m3fn.  Nothing here is
 "parity unpinned".
 """
 
@@ -38,10 +40,11 @@ from .wpinv import wpinv
 from .grad import wprod_grad
 from .deblur import deblur_loss, deblur_grad, deblur_steps
 from .metrics import rel_fro, psnr
+from .quant import e4m3_round, facewise_fp8, wprod_fp8
 
 __all__ = [
     "lift", "ilift", "lift_adjoint", "ilift_adjoint", "split_mallat", "check_levels",
     "dense_lifting_matrix", "facewise", "wprod", "transpose", "identity", "trace",
     "wsvd", "spwsvd", "wpinv", "wprod_grad", "deblur_loss", "deblur_grad",
-    "deblur_steps", "rel_fro", "psnr",
+    "deblur_steps", "rel_fro", "psnr", "e4m3_round", "facewise_fp8", "wprod_fp8",
 ]

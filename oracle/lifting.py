@@ -50,13 +50,15 @@ def split_mallat(y, L):
     return y[:m], details
 
 
-def lift(x, L):
+def lift(x, L, dtype=np.float64):
     """Forward transform W_[L] along axis 0 (Algorithm 1 forward loop, Eq. 1).
 
     x: array (p, ...) with p = 2^L m.  Returns the Mallat-ordered coefficients,
-    same shape, float64.
+    same shape, in `dtype` (float64; float32 only for the FP8 emulation, which
+    needs the single-precision coefficients that a float32 implementation of
+    the same two steps produces: d rounded once, s rounded once).
     """
-    s = np.asarray(x, dtype=np.float64)
+    s = np.asarray(x, dtype=dtype)
     check_levels(s.shape[0], L)
     details = []
     for _j in range(1, L + 1):

@@ -536,6 +536,198 @@ __global__ void __launch_bounds__(256) lift_split_transpose_kernel(const float* 
   }
 }
 
+// ---- FP8 w-product: lift fused into the amax and quantisation passes ------------------
+//
+// The per-slice scale needs the amax of each wavelet-domain slice before any
+// of its elements is quantised, so the spatial operands are read twice:
+//   lift_amax_kernel            lift in registers, per-slice max |W(X)_k| into
+//                               amax (bit patterns, atomicMax); no writes
+//   lift_quant_rows_kernel      lift again, q = e4m3(W(A)_k / s_k), K-major rows
+//   lift_quant_transpose_kernel the same for B, transposed through a
+//                               shared-memory tile to K-major (p, n4, Kp)
+// which moves 2 |X| + |q| bytes per operand instead of the 4 |X| + |q| of a
+// lift into FP32 followed by separate amax and quantisation passes.
+
+// One operand of the FP8 passes: spatial (p, R, C) FP32 in, E4M3 codes q
+// (p, R, Cp) (rows kernel) and the per-slice amax bit patterns (p).
+struct Fp8Operand {
+  const float* in;
+  uint8_t* q;
+  unsigned* amax;
+  int R, C, Cp;
+};
+
+// grid (x, m0 + m1): blockIdx.y < m0 takes tube group y of d0, otherwise
+// group y - m0 of d1; blockIdx.x strides over the group's plane.
+template <int L, int VEC>
+__global__ void __launch_bounds__(256) lift_amax_kernel(Fp8Operand d0, Fp8Operand d1, int64_t p, int m0) {
+  constexpr int G = 1 << L;
+  const bool first = int(blockIdx.y) < m0;
+  const Fp8Operand d = first ? d0 : d1;
+  const int64_t g = first ? blockIdx.y : blockIdx.y - m0;
+  const int64_t plane = int64_t(d.R) * d.C;
+  const int64_t nvec = plane / VEC;
+  float mx[G];
+#pragma unroll
+  for (int t = 0; t < G; ++t) mx[t] = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x) {
+    float v[G][VEC];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const float* src = d.in + (g * G + t) * plane + i * VEC;
+      if constexpr (VEC == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+        v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
+      } else {
+        v[t][0] = __ldg(src);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      float x[G], y[G];
+#pragma unroll
+      for (int t = 0; t < G; ++t) x[t] = v[t][j];
+      lift_group<L>(x, y);
+#pragma unroll
+      for (int t = 0; t < G; ++t) mx[t] = fmaxf(mx[t], fabsf(y[t]));
+    }
+  }
+  __shared__ float red[8][G];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < G; ++t) {
+    float m = mx[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[warp][t] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < G) {
+    float m = red[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w][threadIdx.x]);
+    atomicMax(d.amax + mallat_slice<L>(int(threadIdx.x), g, p), __float_as_uint(m));
+  }
+}
+
+// Spatial A (p, R, C) -> E4M3 codes of W(A) with the slices' scales, K-major
+// rows (p, R, Cp); grid-stride over (tube group, VEC-vector) items.
+template <int L, int VEC>
+__global__ void __launch_bounds__(256) lift_quant_rows_kernel(Fp8Operand d, int64_t p) {
+  constexpr int G = 1 << L;
+  const int64_t plane = int64_t(d.R) * d.C;
+  const int64_t nvec = plane / VEC;
+  const int64_t total = (p >> L) * nvec;
+  for (int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; item < total;
+       item += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = item / nvec;
+    const int64_t e = (item - g * nvec) * VEC;
+    const int r = int(e / d.C), c = int(e - int64_t(r) * d.C);
+    float v[G][VEC];
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const float* src = d.in + (g * G + t) * plane + e;
+      if constexpr (VEC == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+        v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
+      } else {
+        v[t][0] = __ldg(src);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+      float x[G], y[G];
+#pragma unroll
+      for (int t = 0; t < G; ++t) x[t] = v[t][j];
+      lift_group<L>(x, y);
+#pragma unroll
+      for (int t = 0; t < G; ++t) v[t][j] = y[t];
+    }
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int64_t s = mallat_slice<L>(t, g, p);
+      const float inv = 1.f / fp8_scale(__ldg(d.amax + s));
+      uint8_t* o = d.q + (s * d.R + r) * int64_t(d.Cp) + c;
+      if constexpr (VEC == 4) {
+        const uint32_t w = uint32_t(to_e4m3(v[t][0] * inv)) | (uint32_t(to_e4m3(v[t][1] * inv)) << 8) |
+                           (uint32_t(to_e4m3(v[t][2] * inv)) << 16) | (uint32_t(to_e4m3(v[t][3] * inv)) << 24);
+        *reinterpret_cast<uint32_t*>(o) = w;
+      } else {
+        *o = to_e4m3(v[t][0] * inv);
+      }
+    }
+  }
+}
+
+// Tile of lift_quant_transpose_kernel: TR input rows x CW columns of each of
+// the G slices, E = TR * CW elements per slice, at most 68 KB of shared
+// memory (three CTAs per SM) for G >= 8.
+template <int L>
+struct QuantTile {
+  static constexpr int G = 1 << L;
+  static constexpr int E = G >= 32 ? 512 : (G >= 8 ? 1024 : 2048);
+  static constexpr int TR = (512 / G) < 64 ? (512 / G) : 64;
+  static constexpr int CW = E / TR;
+  static constexpr size_t SMEM = size_t(G) * TR * (CW + 1) * sizeof(float);
+};
+
+// Spatial B (p, R, C) -> E4M3 codes of W(B)^T with the slices' scales,
+// K-major (p, C, Rp), Rp a multiple of 16.  Tiled as
+// lift_split_transpose_kernel (loads into shared memory, the lift across the
+// group in registers); every writing thread stores 16 consecutive
+// K-elements of one output row as one 16-byte vector per slice.
+template <int L>
+__global__ void __launch_bounds__(256) lift_quant_transpose_kernel(const float* __restrict__ in,
+                                                                   uint8_t* __restrict__ q,
+                                                                   const unsigned* __restrict__ amax, int64_t p,
+                                                                   int R, int C, int Rp) {
+  constexpr int G = 1 << L;
+  constexpr int E = QuantTile<L>::E, TR = QuantTile<L>::TR, CW = QuantTile<L>::CW;
+  constexpr int PER = E / 256;
+  constexpr int LD = CW + 1;
+  static_assert(TR % 16 == 0, "16-byte output chunks");
+  extern __shared__ float tile[];   // [G][TR][LD]
+  const int c0 = blockIdx.x * CW, r0 = blockIdx.y * TR;
+  const int64_t g = blockIdx.z;
+  const int64_t plane = int64_t(R) * C;
+  const int tid = threadIdx.x;
+#pragma unroll 2
+  for (int t = 0; t < G; ++t) {
+    const float* src = in + (g * G + t) * plane;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int idx = tid + 256 * k, i = idx / CW, j = idx % CW;
+      const int r = r0 + i, c = c0 + j;
+      tile[(t * TR + i) * LD + j] = (r < R && c < C) ? __ldg(src + int64_t(r) * C + c) : 0.f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int idx = tid + 256 * k, i = idx / CW, j = idx % CW;
+    float x[G], y[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) x[t] = tile[(t * TR + i) * LD + j];
+    lift_group<L>(x, y);
+#pragma unroll
+    for (int t = 0; t < G; ++t) tile[(t * TR + i) * LD + j] = y[t];
+  }
+  __syncthreads();
+  const int cl = tid / (TR / 16), chunk = tid % (TR / 16);
+  const int c = c0 + cl, rs = r0 + chunk * 16;
+  if (tid < CW * (TR / 16) && c < C && rs < Rp) {
+#pragma unroll 2
+    for (int t = 0; t < G; ++t) {
+      const int64_t s = mallat_slice<L>(t, g, p);
+      const float inv = 1.f / fp8_scale(__ldg(amax + s));
+      __align__(16) uint8_t b[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) b[k] = to_e4m3(tile[(t * TR + chunk * 16 + k) * LD + cl] * inv);
+      *reinterpret_cast<uint4*>(q + (s * C + c) * int64_t(Rp) + rs) = *reinterpret_cast<const uint4*>(b);
+    }
+  }
+}
+
 namespace tc {
 
 // Slices per store pass of the fused epilogue: the largest power of two <= G
@@ -1157,15 +1349,85 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
   return launch_fused_mc<L, 1, BMN>(mc, mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
 }
 
+// FP8 w-product: amax pass and quantisation passes with the lift folded in,
+// the persistent E4M3 GEMM (scales applied in its epilogue) into the
+// wavelet-domain C_hat, then the inverse transform.
+template <int L>
+static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
+                            void* ws, size_t ws_bytes, cudaStream_t st) {
+  const int64_t m = p >> L, Kp = pad16(n2);
+  Carver cv(ws, ws_bytes);
+  float* Chat = cv.take<float>(size_t(p) * n1 * n4);
+  uint8_t* A8 = cv.take<uint8_t>(size_t(p) * n1 * Kp);
+  uint8_t* B8 = cv.take<uint8_t>(size_t(p) * n4 * Kp);
+  unsigned* amax = cv.take<unsigned>(2 * size_t(p));
+  if (!cv.ok) return WP_ERR_WORKSPACE;
+  WP_CUDA_TRY(cudaMemsetAsync(amax, 0, 2 * size_t(p) * sizeof(unsigned), st));
+  const Fp8Operand da{A, A8, amax, int(n1), int(n2), int(Kp)};
+  const Fp8Operand db{B, nullptr, amax + p, int(n2), int(n4), 0};
+  {
+    // one CTA row per tube group and operand; about 8 CTAs per SM in all
+    // (4-vectors hold 4 G running maxima per thread: scalar loads at L = 5)
+    const bool v4 = L <= 4 && (n2 % 4 == 0) && (n4 % 4 == 0) && aligned16(A) && aligned16(B);
+    const int64_t vec = v4 ? 4 : 1;
+    const int64_t maxx = (std::max(n1 * n2, n2 * n4) / vec + 255) / 256;
+    const int64_t bx = std::max<int64_t>(1, std::min<int64_t>(maxx, (int64_t(sm_count()) * 8 + 2 * m - 1) / (2 * m)));
+    const dim3 grid{unsigned(bx), unsigned(2 * m), 1u};
+    WP_PROFILE("lift_amax_fp8", st);
+    if (v4) lift_amax_kernel<L, 4><<<grid, 256, 0, st>>>(da, db, p, int(m));
+    else lift_amax_kernel<L, 1><<<grid, 256, 0, st>>>(da, db, p, int(m));
+    WP_TRY(launch_status());
+  }
+  {
+    const bool v4 = (n2 % 4 == 0) && aligned16(A);
+    const int64_t total = m * (n1 * n2 / (v4 ? 4 : 1));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
+    WP_PROFILE("lift_quant_fp8", st);
+    if (v4) lift_quant_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(da, p);
+    else lift_quant_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(da, p);
+    WP_TRY(launch_status());
+  }
+  {
+    constexpr int TR = QuantTile<L>::TR, CW = QuantTile<L>::CW;
+    constexpr size_t smem = QuantTile<L>::SMEM;
+    static bool attr = false;
+    if (!attr) {
+      WP_CUDA_TRY(cudaFuncSetAttribute(lift_quant_transpose_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem)));
+      attr = true;
+    }
+    const dim3 grid{unsigned((n4 + CW - 1) / CW), unsigned((Kp + TR - 1) / TR), unsigned(m)};
+    WP_PROFILE("lift_quant_transpose_fp8", st);
+    lift_quant_transpose_kernel<L><<<grid, 256, smem, st>>>(B, B8, amax + p, p, int(n2), int(n4), int(Kp));
+    WP_TRY(launch_status());
+  }
+  CUtensorMap ma, mb;
+  constexpr int BN = 256;
+  WP_TRY(make_map(&ma, A8, n2, Kp, n1, p, tc::BM, 1));
+  WP_TRY(make_map(&mb, B8, n2, Kp, n4, p, BN, 1));
+  WP_TRY((launch_gemm<BN, 8, 4>(ma, ma, mb, mb, Chat, n1, n4, n2, p, st, "tc_gemm_fp8", amax, amax + p)));
+  return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st);
+}
+
 // C = A *w B for tensor-core precisions with the transform fused into the
 // operand preparation and the GEMM epilogue.  WP_ERR_UNSUPPORTED when the
 // arguments fall outside the fused path (the caller then uses the unfused one).
 int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p, int L,
                    int prec, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3) return WP_ERR_UNSUPPORTED;
+  if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3 && prec != WP_PREC_FP8) return WP_ERR_UNSUPPORTED;
   if (L < 1 || L > 5) return WP_ERR_UNSUPPORTED;
   if ((p >> L) > 65535 || p > 65535 || n1 > INT32_MAX || n2 > INT32_MAX || n4 > INT32_MAX) return WP_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
+  if (prec == WP_PREC_FP8) {
+    if (2 * (p >> L) > 65535) return WP_ERR_UNSUPPORTED;
+    switch (L) {
+      case 1: return wprod_fp8_levels<1>(A, B, C, n1, n2, n4, p, ws, ws_bytes, st);
+      case 2: return wprod_fp8_levels<2>(A, B, C, n1, n2, n4, p, ws, ws_bytes, st);
+      case 3: return wprod_fp8_levels<3>(A, B, C, n1, n2, n4, p, ws, ws_bytes, st);
+      case 4: return wprod_fp8_levels<4>(A, B, C, n1, n2, n4, p, ws, ws_bytes, st);
+      default: return wprod_fp8_levels<5>(A, B, C, n1, n2, n4, p, ws, ws_bytes, st);
+    }
+  }
   const int64_t Kp = pad8(n2);
   const bool x3 = (prec == WP_PREC_BF16X3);
   // The inverse-lift epilogue needs all 2^L accumulators of a tile in TMEM,

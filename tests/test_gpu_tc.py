@@ -176,3 +176,53 @@ def test_wprod_fp8_and_backward():
     rA, rB = O.wprod_grad(A, B, G, L)
     assert O.rel_fro(host(dA), rA) <= 0.08 and O.rel_fro(host(dB), rB) <= 0.08
     assert capi.wp_get_device_error() == 0
+
+
+# FP8 against the oracle's E4M3 emulation (same per-slice scales and codes,
+# exact products): the remaining difference is the FP32 accumulation order.
+TOL_FP8_EMU = 1e-6
+
+FP8_WPROD_CASES = [
+    # p, n1, n2, n4, L
+    (16, 64, 80, 48, 4),        # lift-fused FP8 path, 4-vectors
+    (24, 96, 64, 72, 3),        # m = 3 tube groups, ragged N tile
+    (8, 33, 17, 40, 2),         # odd n2: scalar lift, padded K rows
+    (64, 40, 96, 24, 5),        # G = 32: scalar amax pass, 16-row transpose tiles
+    (6, 130, 256, 300, 1),      # L = 1, two M tiles, two N tiles of 256
+]
+
+
+@pytest.mark.parametrize("p,n1,n2,n4,L", FP8_WPROD_CASES)
+def test_wprod_fp8_matches_emulation(p, n1, n2, n4, L):
+    A, B = rand((p, n1, n2), 21), rand((p, n2, n4), 22)
+    C = host(capi.wp_wprod(dev(A), dev(B), L, prec="fp8"))
+    err = O.rel_fro(C, O.wprod_fp8(A, B, L))
+    print(f"fp8 vs emulation {p}x{n1}x{n2}x{n4} L={L}: {err:.2e}")
+    assert err <= TOL_FP8_EMU, err
+    assert O.rel_fro(C, O.wprod(A, B, L)) <= 0.08
+    assert capi.wp_get_device_error() == 0
+
+
+def test_wprod_fp8_scaled_slices_matches_emulation():
+    """Spatial slices scaled by 10^U[-3, 3]: every wavelet slice has its own
+    scale, so every tube group keeps the emulation's accuracy."""
+    A, B = synth.scaled_pair(64, 96, 48, 32, seed=2)
+    C = host(capi.wp_wprod(dev(A), dev(B), 3, prec="fp8"))
+    ref = O.wprod_fp8(A, B, 3)
+    for g in range(4):
+        assert O.rel_fro(C[8 * g:8 * g + 8], ref[8 * g:8 * g + 8]) <= TOL_FP8_EMU
+
+
+@pytest.mark.parametrize("tA,tB", [(False, False), (True, False), (False, True)])
+def test_facewise_and_unfused_wprod_fp8_match_emulation(tA, tB):
+    """The stand-alone FP8 face-product (amax, quantise, GEMM) and the unfused
+    FP8 w-product taken for transposed operands."""
+    p, M, N, K, L = 8, 72, 100, 56, 3
+    A = rand((p, K, M) if tA else (p, M, K), 23)
+    B = rand((p, N, K) if tB else (p, K, N), 24)
+    At = np.swapaxes(A, 1, 2) if tA else A
+    Bt = np.swapaxes(B, 1, 2) if tB else B
+    C = host(capi.wp_facewise(dev(A), dev(B), transA=tA, transB=tB, prec="fp8"))
+    assert O.rel_fro(C, O.facewise_fp8(At, Bt)) <= TOL_FP8_EMU
+    C = host(capi.wp_wprod(dev(A), dev(B), L, transA=tA, transB=tB, prec="fp8"))
+    assert O.rel_fro(C, O.wprod_fp8(np.ascontiguousarray(At), np.ascontiguousarray(Bt), L)) <= TOL_FP8_EMU
