@@ -119,6 +119,20 @@ __device__ __forceinline__ uint8_t to_e4m3(float x) {
   return static_cast<uint8_t>(__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3));
 }
 
+// Four E4M3 codes packed little-endian (a in the lowest byte), converted in pairs.
+__device__ __forceinline__ uint32_t to_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xffffu) | (hi << 16);
+}
+
+// inv[i] = 1 / s_i for the per-slice scales s_i = amax_i / 448 (1 for amax_i = 0).
+__global__ void __launch_bounds__(256) fp8_inv_scales_kernel(const unsigned* __restrict__ amax_bits,
+                                                             float* __restrict__ inv, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) inv[i] = 1.f / fp8_scale(amax_bits[i]);
+}
+
 // in (batch, R, C) fp32 -> q (batch, R, Cp) e4m3 with the slice's scale.
 __global__ void __launch_bounds__(256) quant_rows_kernel(const float* __restrict__ in, uint8_t* __restrict__ q,
                                                          const unsigned* __restrict__ amax_bits, int64_t rows_per_slice,
@@ -393,7 +407,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // For C = A *w B (no transposes, 1 <= L <= 5) the operand preparation and
 // the inverse transform are folded into the neighbouring passes:
 //   lift_split_rows_kernel       spatial A (p, n1, n2) -> W(A) as BF16 hi/lo,
-//                                K-major (p, n1, Kp), Mallat order: one HBM pass
+//                                K-major (p, n1, Kp): one HBM pass
 //   lift_split_transpose_kernel  spatial B (p, n2, n4) -> W(B)^T as BF16 hi/lo,
 //                                K-major (p, n4, Kp), transposed through a
 //                                shared-memory tile: one HBM pass
@@ -405,8 +419,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 //                                registers (Eq. 3) and stores spatial C.  The
 //                                wavelet-domain product never reaches HBM.
 
-// One operand of lift_split_rows_kernel: spatial (p, R, C) in, Mallat-ordered
-// BF16 hi (/ lo) (p, R, Cp) out; `items` = (p / 2^L) * R * C / VEC.
+// The wavelet-domain operands of these kernels, and C_hat on the three-pass
+// path, stay inside one w-product call, so they use the group-interleaved
+// slice order (local index t of tube group g at slice g * 2^L + t, local
+// order s_L, d_L, d_{L-1}, ..., d_1 as in lift_math.cuh): every pass over
+// them streams G consecutive slices per group.  The face-product does not
+// depend on the slice order, and the result C is spatial.
+
+// One operand of lift_split_rows_kernel: spatial (p, R, C) in, wavelet-domain
+// BF16 hi (/ lo) (p, R, Cp) out (group-interleaved); `items` = (p / 2^L) * R * C / VEC.
 struct SplitOperand {
   const float* in;
   __nv_bfloat16* hi;
@@ -445,7 +466,7 @@ __device__ __forceinline__ void lift_split_item(const SplitOperand& d, int64_t p
   }
 #pragma unroll
   for (int t = 0; t < G; ++t) {
-    const int64_t o = mallat_slice<L>(t, g, p) * int64_t(d.R) * d.Cp + int64_t(r) * d.Cp + c;
+    const int64_t o = (g * G + t) * int64_t(d.R) * d.Cp + int64_t(r) * d.Cp + c;
     if constexpr (VEC == 4) {
       __nv_bfloat16 h[4], l[4];
 #pragma unroll
@@ -476,7 +497,8 @@ __global__ void __launch_bounds__(256) lift_split_rows_kernel(SplitOperand d0, S
   }
 }
 
-// Spatial B (p, R, C) -> Mallat-ordered transposed BF16 hi/lo (p, C, Rp).
+// Spatial B (p, R, C) -> transposed wavelet-domain BF16 hi/lo (p, C, Rp),
+// group-interleaved.
 // A CTA (256 threads) takes a TR x CW tile of the plane (TR = min(64, 512/G)
 // input rows, CW = 2048/TR columns) of one tube group: coalesced loads into
 // shared memory, the lift across the group's G slices in registers, then
@@ -525,7 +547,7 @@ __global__ void __launch_bounds__(256) lift_split_transpose_kernel(const float* 
   if (tid < CW * (TR / 8) && c < C && rs < Rp) {
 #pragma unroll 2
     for (int t = 0; t < G; ++t) {
-      const int64_t s = mallat_slice<L>(t, g, p);
+      const int64_t s = g * G + t;
       __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) split_bf16(tile[(t * TR + chunk * 8 + q) * LD + cl], h[q], l[q]);
@@ -548,12 +570,27 @@ __global__ void __launch_bounds__(256) lift_split_transpose_kernel(const float* 
 // which moves 2 |X| + |q| bytes per operand instead of the 4 |X| + |q| of a
 // lift into FP32 followed by separate amax and quantisation passes.
 
+// VEC consecutive floats (16-, 8- or 4-byte aligned load).
+template <int VEC>
+__device__ __forceinline__ void load_floats(const float* src, float* v) {
+  if constexpr (VEC == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (VEC == 2) {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(src));
+    v[0] = q.x; v[1] = q.y;
+  } else {
+    v[0] = __ldg(src);
+  }
+}
+
 // One operand of the FP8 passes: spatial (p, R, C) FP32 in, E4M3 codes q
 // (p, R, Cp) (rows kernel) and the per-slice amax bit patterns (p).
 struct Fp8Operand {
   const float* in;
   uint8_t* q;
   unsigned* amax;
+  const float* inv;     // 1 / s per slice (after the amax pass)
   int R, C, Cp;
 };
 
@@ -573,15 +610,7 @@ __global__ void __launch_bounds__(256) lift_amax_kernel(Fp8Operand d0, Fp8Operan
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nvec; i += int64_t(gridDim.x) * blockDim.x) {
     float v[G][VEC];
 #pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const float* src = d.in + (g * G + t) * plane + i * VEC;
-      if constexpr (VEC == 4) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
-        v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
-      } else {
-        v[t][0] = __ldg(src);
-      }
-    }
+    for (int t = 0; t < G; ++t) load_floats<VEC>(d.in + (g * G + t) * plane + i * VEC, v[t]);
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       float x[G], y[G];
@@ -606,7 +635,7 @@ __global__ void __launch_bounds__(256) lift_amax_kernel(Fp8Operand d0, Fp8Operan
     float m = red[0][threadIdx.x];
 #pragma unroll
     for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w][threadIdx.x]);
-    atomicMax(d.amax + mallat_slice<L>(int(threadIdx.x), g, p), __float_as_uint(m));
+    atomicMax(d.amax + g * G + threadIdx.x, __float_as_uint(m));
   }
 }
 
@@ -625,15 +654,7 @@ __global__ void __launch_bounds__(256) lift_quant_rows_kernel(Fp8Operand d, int6
     const int r = int(e / d.C), c = int(e - int64_t(r) * d.C);
     float v[G][VEC];
 #pragma unroll
-    for (int t = 0; t < G; ++t) {
-      const float* src = d.in + (g * G + t) * plane + e;
-      if constexpr (VEC == 4) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(src));
-        v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
-      } else {
-        v[t][0] = __ldg(src);
-      }
-    }
+    for (int t = 0; t < G; ++t) load_floats<VEC>(d.in + (g * G + t) * plane + e, v[t]);
 #pragma unroll
     for (int j = 0; j < VEC; ++j) {
       float x[G], y[G];
@@ -645,13 +666,14 @@ __global__ void __launch_bounds__(256) lift_quant_rows_kernel(Fp8Operand d, int6
     }
 #pragma unroll
     for (int t = 0; t < G; ++t) {
-      const int64_t s = mallat_slice<L>(t, g, p);
-      const float inv = 1.f / fp8_scale(__ldg(d.amax + s));
+      const int64_t s = g * G + t;
+      const float inv = __ldg(d.inv + s);
       uint8_t* o = d.q + (s * d.R + r) * int64_t(d.Cp) + c;
       if constexpr (VEC == 4) {
-        const uint32_t w = uint32_t(to_e4m3(v[t][0] * inv)) | (uint32_t(to_e4m3(v[t][1] * inv)) << 8) |
-                           (uint32_t(to_e4m3(v[t][2] * inv)) << 16) | (uint32_t(to_e4m3(v[t][3] * inv)) << 24);
-        *reinterpret_cast<uint32_t*>(o) = w;
+        *reinterpret_cast<uint32_t*>(o) = to_e4m3x4(v[t][0] * inv, v[t][1] * inv, v[t][2] * inv, v[t][3] * inv);
+      } else if constexpr (VEC == 2) {
+        *reinterpret_cast<uint16_t*>(o) =
+            uint16_t(__nv_cvt_float2_to_fp8x2(make_float2(v[t][0] * inv, v[t][1] * inv), __NV_SATFINITE, __NV_E4M3));
       } else {
         *o = to_e4m3(v[t][0] * inv);
       }
@@ -679,26 +701,46 @@ struct QuantTile {
 template <int L>
 __global__ void __launch_bounds__(256) lift_quant_transpose_kernel(const float* __restrict__ in,
                                                                    uint8_t* __restrict__ q,
-                                                                   const unsigned* __restrict__ amax, int64_t p,
-                                                                   int R, int C, int Rp) {
+                                                                   const float* __restrict__ inv_scale, int R,
+                                                                   int C, int Rp, int vec4) {
   constexpr int G = 1 << L;
   constexpr int E = QuantTile<L>::E, TR = QuantTile<L>::TR, CW = QuantTile<L>::CW;
   constexpr int PER = E / 256;
   constexpr int LD = CW + 1;
-  static_assert(TR % 16 == 0, "16-byte output chunks");
+  constexpr int V4 = E / 4;                     // 4-float loads per slice tile
+  constexpr int PER4 = (V4 + 255) / 256;
+  constexpr int CH = TR / 16;                   // 16-row output chunks per column
+  constexpr int TASKS = G * CW * CH;            // (slice, column, chunk) writes
+  static_assert(TR % 16 == 0 && CW % 4 == 0, "tile shape");
   extern __shared__ float tile[];   // [G][TR][LD]
   const int c0 = blockIdx.x * CW, r0 = blockIdx.y * TR;
   const int64_t g = blockIdx.z;
   const int64_t plane = int64_t(R) * C;
   const int tid = threadIdx.x;
-#pragma unroll 2
+#pragma unroll 8
   for (int t = 0; t < G; ++t) {
     const float* src = in + (g * G + t) * plane;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int idx = tid + 256 * k, i = idx / CW, j = idx % CW;
-      const int r = r0 + i, c = c0 + j;
-      tile[(t * TR + i) * LD + j] = (r < R && c < C) ? __ldg(src + int64_t(r) * C + c) : 0.f;
+    for (int k = 0; k < PER4; ++k) {
+      const int idx = tid + 256 * k;
+      if (V4 % 256 == 0 || idx < V4) {
+        const int i = idx / (CW / 4), j = (idx % (CW / 4)) * 4;
+        const int r = r0 + i, c = c0 + j;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < R) {
+          const float* a = src + int64_t(r) * C + c;
+          if (vec4 && c + 3 < C) {
+            v = __ldg(reinterpret_cast<const float4*>(a));
+          } else {
+            if (c < C) v.x = __ldg(a);
+            if (c + 1 < C) v.y = __ldg(a + 1);
+            if (c + 2 < C) v.z = __ldg(a + 2);
+            if (c + 3 < C) v.w = __ldg(a + 3);
+          }
+        }
+        float* d = tile + (t * TR + i) * LD + j;
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+      }
     }
   }
   __syncthreads();
@@ -713,17 +755,20 @@ __global__ void __launch_bounds__(256) lift_quant_transpose_kernel(const float* 
     for (int t = 0; t < G; ++t) tile[(t * TR + i) * LD + j] = y[t];
   }
   __syncthreads();
-  const int cl = tid / (TR / 16), chunk = tid % (TR / 16);
-  const int c = c0 + cl, rs = r0 + chunk * 16;
-  if (tid < CW * (TR / 16) && c < C && rs < Rp) {
-#pragma unroll 2
-    for (int t = 0; t < G; ++t) {
-      const int64_t s = mallat_slice<L>(t, g, p);
-      const float inv = 1.f / fp8_scale(__ldg(amax + s));
-      __align__(16) uint8_t b[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) b[k] = to_e4m3(tile[(t * TR + chunk * 16 + k) * LD + cl] * inv);
-      *reinterpret_cast<uint4*>(q + (s * C + c) * int64_t(Rp) + rs) = *reinterpret_cast<const uint4*>(b);
+  for (int w = tid; w < TASKS; w += 256) {
+    const int t = w / (CW * CH), rem = w % (CW * CH);
+    const int cl = rem / CH, chunk = rem % CH;
+    const int c = c0 + cl, rs = r0 + chunk * 16;
+    if (c < C && rs < Rp) {
+      const int64_t s = g * G + t;
+      const float inv = __ldg(inv_scale + s);
+      const float* col = tile + (t * TR + chunk * 16) * LD + cl;
+      uint4 b;
+      b.x = to_e4m3x4(col[0 * LD] * inv, col[1 * LD] * inv, col[2 * LD] * inv, col[3 * LD] * inv);
+      b.y = to_e4m3x4(col[4 * LD] * inv, col[5 * LD] * inv, col[6 * LD] * inv, col[7 * LD] * inv);
+      b.z = to_e4m3x4(col[8 * LD] * inv, col[9 * LD] * inv, col[10 * LD] * inv, col[11 * LD] * inv);
+      b.w = to_e4m3x4(col[12 * LD] * inv, col[13 * LD] * inv, col[14 * LD] * inv, col[15 * LD] * inv);
+      *reinterpret_cast<uint4*>(q + (s * C + c) * int64_t(Rp) + rs) = b;
     }
   }
 }
@@ -821,7 +866,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int it = 0; it < iters && ok; ++it) {
       const int s = it % STAGES;
       const int t = it / nk, kb = it % nk;
-      const int z = int(mallat_slice<L>(t, g, p));
+      const int z = int(g * G + t);
       if (it >= STAGES) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
       if (!ok) break;
       ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
@@ -1322,7 +1367,7 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
     } else {
       WP_TRY((launch_gemm<256, 1, 4, true>(mah, mah, mbh, mbh, Chat, n1, n4, n2, p, st, "tc_gemm_bf16")));
     }
-    return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st);
+    return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st, true);
   }
   constexpr int BN = tc::FusedLayout<L, 1, 1, 512>::BN;
   constexpr bool BMN = (L <= 3);
@@ -1349,6 +1394,16 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
   return launch_fused_mc<L, 1, BMN>(mc, mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
 }
 
+// Elements per thread of the FP8 lift passes: G x VEC values stay in
+// registers, so the vector narrows as the group grows (4 up to L = 3, 2 at
+// L = 4, 1 at L = 5), as far as the row length and alignment allow.
+template <int L>
+static int fp8_vec(bool four_ok, bool two_ok) {
+  if (L <= 3 && four_ok) return 4;
+  if (L <= 4 && two_ok) return 2;
+  return 1;
+}
+
 // FP8 w-product: amax pass and quantisation passes with the lift folded in,
 // the persistent E4M3 GEMM (scales applied in its epilogue) into the
 // wavelet-domain C_hat, then the inverse transform.
@@ -1361,30 +1416,46 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
   uint8_t* A8 = cv.take<uint8_t>(size_t(p) * n1 * Kp);
   uint8_t* B8 = cv.take<uint8_t>(size_t(p) * n4 * Kp);
   unsigned* amax = cv.take<unsigned>(2 * size_t(p));
+  float* inv = cv.take<float>(2 * size_t(p));
   if (!cv.ok) return WP_ERR_WORKSPACE;
   WP_CUDA_TRY(cudaMemsetAsync(amax, 0, 2 * size_t(p) * sizeof(unsigned), st));
-  const Fp8Operand da{A, A8, amax, int(n1), int(n2), int(Kp)};
-  const Fp8Operand db{B, nullptr, amax + p, int(n2), int(n4), 0};
+  const Fp8Operand da{A, A8, amax, inv, int(n1), int(n2), int(Kp)};
+  const Fp8Operand db{B, nullptr, amax + p, inv + p, int(n2), int(n4), 0};
   {
     // one CTA row per tube group and operand; about 8 CTAs per SM in all
-    // (4-vectors hold 4 G running maxima per thread: scalar loads at L = 5)
-    const bool v4 = L <= 4 && (n2 % 4 == 0) && (n4 % 4 == 0) && aligned16(A) && aligned16(B);
-    const int64_t vec = v4 ? 4 : 1;
+    // both operands' rows must allow the vector width (A rows n2, B rows n4)
+    const int vec = fp8_vec<L>(n2 % 4 == 0 && n4 % 4 == 0 && aligned16(A) && aligned16(B),
+                               n2 % 2 == 0 && n4 % 2 == 0);
     const int64_t maxx = (std::max(n1 * n2, n2 * n4) / vec + 255) / 256;
     const int64_t bx = std::max<int64_t>(1, std::min<int64_t>(maxx, (int64_t(sm_count()) * 8 + 2 * m - 1) / (2 * m)));
     const dim3 grid{unsigned(bx), unsigned(2 * m), 1u};
     WP_PROFILE("lift_amax_fp8", st);
-    if (v4) lift_amax_kernel<L, 4><<<grid, 256, 0, st>>>(da, db, p, int(m));
-    else lift_amax_kernel<L, 1><<<grid, 256, 0, st>>>(da, db, p, int(m));
+    if constexpr (L <= 3) {
+      if (vec == 4) lift_amax_kernel<L, 4><<<grid, 256, 0, st>>>(da, db, p, int(m));
+    }
+    if constexpr (L <= 4) {
+      if (vec == 2) lift_amax_kernel<L, 2><<<grid, 256, 0, st>>>(da, db, p, int(m));
+    }
+    if (vec == 1) lift_amax_kernel<L, 1><<<grid, 256, 0, st>>>(da, db, p, int(m));
     WP_TRY(launch_status());
   }
   {
-    const bool v4 = (n2 % 4 == 0) && aligned16(A);
-    const int64_t total = m * (n1 * n2 / (v4 ? 4 : 1));
+    WP_PROFILE("fp8_scales", st);
+    fp8_inv_scales_kernel<<<unsigned((2 * p + 255) / 256), 256, 0, st>>>(amax, inv, int(2 * p));
+    WP_TRY(launch_status());
+  }
+  {
+    const int vec = fp8_vec<L>(n2 % 4 == 0 && aligned16(A), n2 % 2 == 0);
+    const int64_t total = m * (n1 * n2 / vec);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
     WP_PROFILE("lift_quant_fp8", st);
-    if (v4) lift_quant_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(da, p);
-    else lift_quant_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(da, p);
+    if constexpr (L <= 3) {
+      if (vec == 4) lift_quant_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(da, p);
+    }
+    if constexpr (L <= 4) {
+      if (vec == 2) lift_quant_rows_kernel<L, 2><<<unsigned(blocks), 256, 0, st>>>(da, p);
+    }
+    if (vec == 1) lift_quant_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(da, p);
     WP_TRY(launch_status());
   }
   {
@@ -1398,7 +1469,8 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
     }
     const dim3 grid{unsigned((n4 + CW - 1) / CW), unsigned((Kp + TR - 1) / TR), unsigned(m)};
     WP_PROFILE("lift_quant_transpose_fp8", st);
-    lift_quant_transpose_kernel<L><<<grid, 256, smem, st>>>(B, B8, amax + p, p, int(n2), int(n4), int(Kp));
+    const int vec4 = (n4 % 4 == 0) && aligned16(B);
+    lift_quant_transpose_kernel<L><<<grid, 256, smem, st>>>(B, B8, inv + p, int(n2), int(n4), int(Kp), vec4);
     WP_TRY(launch_status());
   }
   CUtensorMap ma, mb;
@@ -1406,7 +1478,7 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
   WP_TRY(make_map(&ma, A8, n2, Kp, n1, p, tc::BM, 1));
   WP_TRY(make_map(&mb, B8, n2, Kp, n4, p, BN, 1));
   WP_TRY((launch_gemm<BN, 8, 4>(ma, ma, mb, mb, Chat, n1, n4, n2, p, st, "tc_gemm_fp8", amax, amax + p)));
-  return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st);
+  return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st, true);
 }
 
 // C = A *w B for tensor-core precisions with the transform fused into the

@@ -7,9 +7,13 @@ namespace wp {
 
 enum LiftOpId { LIFT_FWD = 0, LIFT_INV = 1, LIFT_ADJ = 2, LIFT_IADJ = 3 };
 
-// Fused L-level lifting of a (p, plane) tensor; see lift.cu.
+// Fused L-level lifting of a (p, plane) tensor; see lift.cu.  `interleaved`:
+// the wavelet-domain side uses the group-interleaved slice order (local index
+// t of tube group g at slice g * 2^L + t) instead of the Mallat order; only
+// for L <= kMaxInterleavedLevels (WP_ERR_UNSUPPORTED beyond).
+constexpr int kMaxInterleavedLevels = 5;
 int lift_dispatch(int op, const float* in, float* out, int64_t plane, int64_t p, int L,
-                  cudaStream_t st);
+                  cudaStream_t st, bool interleaved = false);
 
 // Plain FP32 SIMT batched GEMM; see gemm_simt.cu.
 int sgemm_batched(const float* A, const float* B, float* C, int M, int N, int K, bool transA,

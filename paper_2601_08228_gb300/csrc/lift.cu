@@ -11,6 +11,15 @@
 //
 // For L > 5 the group no longer fits in registers; a shared-memory variant
 // stages a (G x E)-element tile and lifts level by level.
+//
+// Wavelet-side slice order.  The exported transforms use the Mallat order of
+// Eq. (1).  Buffers that stay inside one library call (the w-product's
+// W(A), W(B), C_hat and the backward's cotangents) may instead use the
+// group-interleaved order, local index t of group g at slice g * 2^L + t:
+// a pass over it reads and writes G consecutive slices per group.  Reading
+// the Mallat positions of a group (slices g, m + g, 2m + 2g, ...) streams at
+// about half the copy rate on GB300 at L = 4 (measured: 3.5 vs 6.6 TB/s for
+// the same bytes), so the internal round trips avoid it.
 
 #include <algorithm>
 
@@ -69,7 +78,7 @@ __device__ __forceinline__ void store_vec(float* p, const float* v) {
 // Launched with programmatic serialisation: it may start while the previous
 // kernel of the stream finishes and waits for that kernel's completion before
 // reading; it lets its own successor start early the same way.
-template <int L, int VEC, int OP>
+template <int L, int VEC, int OP, bool IL>
 __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__ in,
                                                        float* __restrict__ out, int64_t plane,
                                                        int64_t p, int64_t nvec, int64_t total) {
@@ -83,7 +92,7 @@ __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__
     float v[G][VEC];
 #pragma unroll
     for (int t = 0; t < G; ++t) {
-      const int64_t slice = reads_spatial(OP) ? g * G + t : mallat_slice<L>(t, g, p);
+      const int64_t slice = (reads_spatial(OP) || IL) ? g * G + t : mallat_slice<L>(t, g, p);
       load_vec<VEC>(in + slice * plane + e, v[t]);
     }
     float w[G][VEC];
@@ -98,7 +107,7 @@ __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__
     }
 #pragma unroll
     for (int t = 0; t < G; ++t) {
-      const int64_t slice = reads_spatial(OP) ? mallat_slice<L>(t, g, p) : g * G + t;
+      const int64_t slice = (reads_spatial(OP) && !IL) ? mallat_slice<L>(t, g, p) : g * G + t;
       store_vec<VEC>(out + slice * plane + e, w[t]);
     }
   }
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(256) lift_smem_kernel(const float* __restrict_
   }
 }
 
-template <int L, int VEC, int OP>
+template <int L, int VEC, int OP, bool IL>
 static int launch_reg(const float* in, float* out, int64_t plane, int64_t p, cudaStream_t st) {
   const int64_t nvec = plane / VEC;
   const int64_t total = (p >> L) * nvec;
@@ -199,7 +208,7 @@ static int launch_reg(const float* in, float* out, int64_t plane, int64_t p, cud
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   WP_PROFILE(kLiftNames[OP], st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP>, in, out, plane, p, nvec, total));
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP, IL>, in, out, plane, p, nvec, total));
   return launch_status();
 }
 
@@ -234,29 +243,37 @@ static int launch_smem(const float* in, float* out, int64_t plane, int64_t p, in
                   : launch_smem_e<OP, 16>(in, out, plane, p, L, st);
 }
 
-template <int OP>
+template <int OP, bool IL>
 static int dispatch(const float* in, float* out, int64_t plane, int64_t p, int L, cudaStream_t st) {
   const bool v4 = (plane % 4 == 0) && aligned16(in) && aligned16(out);
   const bool v2 = (plane % 2 == 0);
   switch (L) {
-    case 0: return v4 ? launch_reg<0, 4, OP>(in, out, plane, p, st) : launch_reg<0, 1, OP>(in, out, plane, p, st);
-    case 1: return v4 ? launch_reg<1, 4, OP>(in, out, plane, p, st) : launch_reg<1, 1, OP>(in, out, plane, p, st);
-    case 2: return v4 ? launch_reg<2, 4, OP>(in, out, plane, p, st) : launch_reg<2, 1, OP>(in, out, plane, p, st);
-    case 3: return v4 ? launch_reg<3, 4, OP>(in, out, plane, p, st) : launch_reg<3, 1, OP>(in, out, plane, p, st);
-    case 4: return v4 ? launch_reg<4, 4, OP>(in, out, plane, p, st) : launch_reg<4, 1, OP>(in, out, plane, p, st);
-    case 5: return v2 ? launch_reg<5, 2, OP>(in, out, plane, p, st) : launch_reg<5, 1, OP>(in, out, plane, p, st);
-    default: return launch_smem<OP>(in, out, plane, p, L, st);
+    case 0: return v4 ? launch_reg<0, 4, OP, IL>(in, out, plane, p, st) : launch_reg<0, 1, OP, IL>(in, out, plane, p, st);
+    case 1: return v4 ? launch_reg<1, 4, OP, IL>(in, out, plane, p, st) : launch_reg<1, 1, OP, IL>(in, out, plane, p, st);
+    case 2: return v4 ? launch_reg<2, 4, OP, IL>(in, out, plane, p, st) : launch_reg<2, 1, OP, IL>(in, out, plane, p, st);
+    case 3: return v4 ? launch_reg<3, 4, OP, IL>(in, out, plane, p, st) : launch_reg<3, 1, OP, IL>(in, out, plane, p, st);
+    case 4: return v4 ? launch_reg<4, 4, OP, IL>(in, out, plane, p, st) : launch_reg<4, 1, OP, IL>(in, out, plane, p, st);
+    case 5: return v2 ? launch_reg<5, 2, OP, IL>(in, out, plane, p, st) : launch_reg<5, 1, OP, IL>(in, out, plane, p, st);
+    default:
+      if (IL) return WP_ERR_UNSUPPORTED;
+      return launch_smem<OP>(in, out, plane, p, L, st);
   }
 }
 
-int lift_dispatch(int op, const float* in, float* out, int64_t plane, int64_t p, int L,
-                  cudaStream_t st) {
+template <bool IL>
+static int dispatch_op(int op, const float* in, float* out, int64_t plane, int64_t p, int L, cudaStream_t st) {
   switch (op) {
-    case OP_FWD: return dispatch<OP_FWD>(in, out, plane, p, L, st);
-    case OP_INV: return dispatch<OP_INV>(in, out, plane, p, L, st);
-    case OP_ADJ: return dispatch<OP_ADJ>(in, out, plane, p, L, st);
-    default: return dispatch<OP_IADJ>(in, out, plane, p, L, st);
+    case OP_FWD: return dispatch<OP_FWD, IL>(in, out, plane, p, L, st);
+    case OP_INV: return dispatch<OP_INV, IL>(in, out, plane, p, L, st);
+    case OP_ADJ: return dispatch<OP_ADJ, IL>(in, out, plane, p, L, st);
+    default: return dispatch<OP_IADJ, IL>(in, out, plane, p, L, st);
   }
+}
+
+int lift_dispatch(int op, const float* in, float* out, int64_t plane, int64_t p, int L, cudaStream_t st,
+                  bool interleaved) {
+  return interleaved ? dispatch_op<true>(op, in, out, plane, p, L, st)
+                     : dispatch_op<false>(op, in, out, plane, p, L, st);
 }
 
 static int lift_entry(int op, const float* in, float* out, int64_t n1, int64_t n2, int64_t p,

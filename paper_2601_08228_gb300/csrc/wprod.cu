@@ -108,10 +108,12 @@ extern "C" int wp_wprod(const float* A, const float* B, float* C, int64_t n1, in
   void* fw = fws ? cv.take<char>(fws) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
-  WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, n1 * n2, p, L, st));
-  WP_TRY(lift_dispatch(LIFT_FWD, B, Bh, n2 * n4, p, L, st));
+  // A_hat, B_hat and C_hat never leave this call: group-interleaved order
+  const bool il = L <= kMaxInterleavedLevels;
+  WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, n1 * n2, p, L, st, il));
+  WP_TRY(lift_dispatch(LIFT_FWD, B, Bh, n2 * n4, p, L, st, il));
   WP_TRY(facewise_run(Ah, Bh, Ch, n1, n2, n4, p, transA != 0, transB != 0, prec, fw, fws, st));
-  return lift_dispatch(LIFT_INV, Ch, C, n1 * n4, p, L, st);
+  return lift_dispatch(LIFT_INV, Ch, C, n1 * n4, p, L, st, il);
 }
 
 static void backward_layout(int64_t n1, int64_t n2, int64_t n4, int64_t p, int prec, Sizer& s) {
@@ -163,18 +165,20 @@ extern "C" int wp_wprod_backward(const float* A, const float* B, const float* G,
   void* fw = fws ? cv.take<char>(fws) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
-  WP_TRY(lift_dispatch(LIFT_IADJ, G, Gh, n1 * n4, p, L, st));
+  // the wavelet-domain intermediates never leave this call: group-interleaved order
+  const bool il = L <= kMaxInterleavedLevels;
+  WP_TRY(lift_dispatch(LIFT_IADJ, G, Gh, n1 * n4, p, L, st, il));
   if (dA) {
     // dA_hat_k = G_hat_k B_hat_k^T: (n1 x n4) (n4 x n2)
-    WP_TRY(lift_dispatch(LIFT_FWD, B, Bh, n2 * n4, p, L, st));
+    WP_TRY(lift_dispatch(LIFT_FWD, B, Bh, n2 * n4, p, L, st, il));
     WP_TRY(facewise_run(Gh, Bh, dXh, n1, n4, n2, p, false, true, prec, fw, fws, st));
-    WP_TRY(lift_dispatch(LIFT_ADJ, dXh, dA, n1 * n2, p, L, st));
+    WP_TRY(lift_dispatch(LIFT_ADJ, dXh, dA, n1 * n2, p, L, st, il));
   }
   if (dB) {
     // dB_hat_k = A_hat_k^T G_hat_k: (n2 x n1) (n1 x n4)
-    WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, n1 * n2, p, L, st));
+    WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, n1 * n2, p, L, st, il));
     WP_TRY(facewise_run(Ah, Gh, dXh, n2, n1, n4, p, true, false, prec, fw, fws, st));
-    WP_TRY(lift_dispatch(LIFT_ADJ, dXh, dB, n2 * n4, p, L, st));
+    WP_TRY(lift_dispatch(LIFT_ADJ, dXh, dB, n2 * n4, p, L, st, il));
   }
   return WP_OK;
 }
