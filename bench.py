@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
-    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "wprod", "jacobi", "batched"],
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "wprod", "wprod_fp8", "jacobi", "batched"],
                     default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
@@ -587,6 +587,10 @@ def run_profile_case(case):
     elif case == "wprod":
         A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
         capi.wp_wprod(A, B, WORKLOAD["L"], prec="bf16x3")
+    elif case == "wprod_fp8":
+        # the precision study's slice shapes at 64 slices (A 268 MB, B 134 MB), L = 4
+        A, B = synth.scaled_pair(1024, 1024, 512, 64, seed=0)
+        capi.wp_wprod(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 4, prec="fp8")
     elif case == "jacobi":
         # 72 slices of 256 x 256: 2-CTA clusters as in the full workload, one wave
         A = torch.from_numpy(synth.hsi_cube(256, 256, 72, seed=0, dtype=np.float32)).cuda()

@@ -562,13 +562,17 @@ __global__ void __launch_bounds__(256) lift_split_transpose_kernel(const float* 
 //
 // The per-slice scale needs the amax of each wavelet-domain slice before any
 // of its elements is quantised, so the spatial operands are read twice:
-//   lift_amax_kernel            lift in registers, per-slice max |W(X)_k| into
-//                               amax (bit patterns, atomicMax); no writes
-//   lift_quant_rows_kernel      lift again, q = e4m3(W(A)_k / s_k), K-major rows
-//   lift_quant_transpose_kernel the same for B, transposed through a
-//                               shared-memory tile to K-major (p, n4, Kp)
-// which moves 2 |X| + |q| bytes per operand instead of the 4 |X| + |q| of a
-// lift into FP32 followed by separate amax and quantisation passes.
+//   lift_amax_kernel        lift A and B in registers, per-slice max |W(X)_k|
+//                           into amax (bit patterns, atomicMax); no writes
+//   fp8_inv_scales_kernel   1 / s_k for every slice, once
+//   lift_quant_rows_kernel  lift again, q = e4m3(W(X)_k / s_k) in row order:
+//                           A K-major (p, n1, Kp), B (p, n2, n4)
+//   transpose_bytes_kernel  B's codes to K-major (p, n4, Kp)
+// which moves 2 |X| + |q| (+ 2 |q_B|) bytes per operand instead of the
+// 4 |X| + |q| of a lift into FP32 followed by separate amax and
+// quantisation passes.  A lift-and-transpose in one pass (shared-memory tile
+// of all 2^L slices) was measured slower than the row pass plus the byte
+// transpose: its load, lift and store phases serialise within a CTA.
 
 // VEC consecutive floats (16-, 8- or 4-byte aligned load).
 template <int VEC>
@@ -639,16 +643,21 @@ __global__ void __launch_bounds__(256) lift_amax_kernel(Fp8Operand d0, Fp8Operan
   }
 }
 
-// Spatial A (p, R, C) -> E4M3 codes of W(A) with the slices' scales, K-major
-// rows (p, R, Cp); grid-stride over (tube group, VEC-vector) items.
+// Spatial X (p, R, C) -> E4M3 codes of W(X) with the slices' scales in row
+// order (p, R, Cp), for two operands in one grid-stride launch over
+// (operand, tube group, VEC-vector) items.
 template <int L, int VEC>
-__global__ void __launch_bounds__(256) lift_quant_rows_kernel(Fp8Operand d, int64_t p) {
+__global__ void __launch_bounds__(256) lift_quant_rows_kernel(Fp8Operand d0, Fp8Operand d1, int64_t p) {
   constexpr int G = 1 << L;
-  const int64_t plane = int64_t(d.R) * d.C;
-  const int64_t nvec = plane / VEC;
-  const int64_t total = (p >> L) * nvec;
-  for (int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; item < total;
-       item += int64_t(gridDim.x) * blockDim.x) {
+  const int64_t items0 = (p >> L) * (int64_t(d0.R) * d0.C / VEC);
+  const int64_t total = items0 + (p >> L) * (int64_t(d1.R) * d1.C / VEC);
+  for (int64_t it = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; it < total;
+       it += int64_t(gridDim.x) * blockDim.x) {
+    const bool first = it < items0;
+    const Fp8Operand d = first ? d0 : d1;
+    const int64_t item = first ? it : it - items0;
+    const int64_t plane = int64_t(d.R) * d.C;
+    const int64_t nvec = plane / VEC;
     const int64_t g = item / nvec;
     const int64_t e = (item - g * nvec) * VEC;
     const int r = int(e / d.C), c = int(e - int64_t(r) * d.C);
@@ -681,95 +690,45 @@ __global__ void __launch_bounds__(256) lift_quant_rows_kernel(Fp8Operand d, int6
   }
 }
 
-// Tile of lift_quant_transpose_kernel: TR input rows x CW columns of each of
-// the G slices, E = TR * CW elements per slice, at most 68 KB of shared
-// memory (three CTAs per SM) for G >= 8.
-template <int L>
-struct QuantTile {
-  static constexpr int G = 1 << L;
-  static constexpr int E = G >= 32 ? 512 : (G >= 8 ? 1024 : 2048);
-  static constexpr int TR = (512 / G) < 64 ? (512 / G) : 64;
-  static constexpr int CW = E / TR;
-  static constexpr size_t SMEM = size_t(G) * TR * (CW + 1) * sizeof(float);
-};
-
-// Spatial B (p, R, C) -> E4M3 codes of W(B)^T with the slices' scales,
-// K-major (p, C, Rp), Rp a multiple of 16.  Tiled as
-// lift_split_transpose_kernel (loads into shared memory, the lift across the
-// group in registers); every writing thread stores 16 consecutive
-// K-elements of one output row as one 16-byte vector per slice.
-template <int L>
-__global__ void __launch_bounds__(256) lift_quant_transpose_kernel(const float* __restrict__ in,
-                                                                   uint8_t* __restrict__ q,
-                                                                   const float* __restrict__ inv_scale, int R,
-                                                                   int C, int Rp, int vec4) {
-  constexpr int G = 1 << L;
-  constexpr int E = QuantTile<L>::E, TR = QuantTile<L>::TR, CW = QuantTile<L>::CW;
-  constexpr int PER = E / 256;
-  constexpr int LD = CW + 1;
-  constexpr int V4 = E / 4;                     // 4-float loads per slice tile
-  constexpr int PER4 = (V4 + 255) / 256;
-  constexpr int CH = TR / 16;                   // 16-row output chunks per column
-  constexpr int TASKS = G * CW * CH;            // (slice, column, chunk) writes
-  static_assert(TR % 16 == 0 && CW % 4 == 0, "tile shape");
-  extern __shared__ float tile[];   // [G][TR][LD]
-  const int c0 = blockIdx.x * CW, r0 = blockIdx.y * TR;
-  const int64_t g = blockIdx.z;
-  const int64_t plane = int64_t(R) * C;
+// E4M3 codes (batch, R, C) -> (batch, C, Rp), Rp a multiple of 16: 64 x 64
+// byte tiles through shared memory.  Loads take 16 bytes per thread along a
+// row; every thread then gathers 16 consecutive K-bytes of one output row
+// (the 32 lanes of a warp on 32 different rows, so their shared-memory
+// reads hit distinct words or broadcast) and stores them as one 16-byte
+// vector.  Output rows beyond R (padding up to Rp) receive zeros.
+__global__ void __launch_bounds__(256) transpose_bytes_kernel(const uint8_t* __restrict__ in,
+                                                              uint8_t* __restrict__ out, int R, int C, int Rp,
+                                                              int vec16) {
+  constexpr int T = 64, S = 80;   // tile edge, shared row stride (16-byte aligned)
+  __shared__ __align__(16) uint8_t tile[T * S];
+  const int c0 = blockIdx.x * T, r0 = blockIdx.y * T;
+  const int64_t b = blockIdx.z;
   const int tid = threadIdx.x;
-#pragma unroll 8
-  for (int t = 0; t < G; ++t) {
-    const float* src = in + (g * G + t) * plane;
+  {
+    const int i = tid >> 2, j = (tid & 3) * 16;
+    const int r = r0 + i, c = c0 + j;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < R) {
+      const uint8_t* src = in + (b * R + r) * int64_t(C) + c;
+      if (vec16 && c + 15 < C) {
+        v = __ldg(reinterpret_cast<const uint4*>(src));
+      } else {
+        uint8_t t[16];
 #pragma unroll
-    for (int k = 0; k < PER4; ++k) {
-      const int idx = tid + 256 * k;
-      if (V4 % 256 == 0 || idx < V4) {
-        const int i = idx / (CW / 4), j = (idx % (CW / 4)) * 4;
-        const int r = r0 + i, c = c0 + j;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < R) {
-          const float* a = src + int64_t(r) * C + c;
-          if (vec4 && c + 3 < C) {
-            v = __ldg(reinterpret_cast<const float4*>(a));
-          } else {
-            if (c < C) v.x = __ldg(a);
-            if (c + 1 < C) v.y = __ldg(a + 1);
-            if (c + 2 < C) v.z = __ldg(a + 2);
-            if (c + 3 < C) v.w = __ldg(a + 3);
-          }
-        }
-        float* d = tile + (t * TR + i) * LD + j;
-        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+        for (int k = 0; k < 16; ++k) t[k] = (c + k < C) ? src[k] : uint8_t(0);
+        v = *reinterpret_cast<const uint4*>(t);
       }
     }
+    *reinterpret_cast<uint4*>(tile + i * S + j) = v;
   }
   __syncthreads();
+  const int cc = tid & 63, k = tid >> 6;
+  const int c = c0 + cc, rs = r0 + k * 16;
+  if (c < C && rs < Rp) {
+    __align__(16) uint8_t t[16];
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int idx = tid + 256 * k, i = idx / CW, j = idx % CW;
-    float x[G], y[G];
-#pragma unroll
-    for (int t = 0; t < G; ++t) x[t] = tile[(t * TR + i) * LD + j];
-    lift_group<L>(x, y);
-#pragma unroll
-    for (int t = 0; t < G; ++t) tile[(t * TR + i) * LD + j] = y[t];
-  }
-  __syncthreads();
-  for (int w = tid; w < TASKS; w += 256) {
-    const int t = w / (CW * CH), rem = w % (CW * CH);
-    const int cl = rem / CH, chunk = rem % CH;
-    const int c = c0 + cl, rs = r0 + chunk * 16;
-    if (c < C && rs < Rp) {
-      const int64_t s = g * G + t;
-      const float inv = __ldg(inv_scale + s);
-      const float* col = tile + (t * TR + chunk * 16) * LD + cl;
-      uint4 b;
-      b.x = to_e4m3x4(col[0 * LD] * inv, col[1 * LD] * inv, col[2 * LD] * inv, col[3 * LD] * inv);
-      b.y = to_e4m3x4(col[4 * LD] * inv, col[5 * LD] * inv, col[6 * LD] * inv, col[7 * LD] * inv);
-      b.z = to_e4m3x4(col[8 * LD] * inv, col[9 * LD] * inv, col[10 * LD] * inv, col[11 * LD] * inv);
-      b.w = to_e4m3x4(col[12 * LD] * inv, col[13 * LD] * inv, col[14 * LD] * inv, col[15 * LD] * inv);
-      *reinterpret_cast<uint4*>(q + (s * C + c) * int64_t(Rp) + rs) = b;
-    }
+    for (int q = 0; q < 16; ++q) t[q] = tile[(k * 16 + q) * S + cc];
+    *reinterpret_cast<uint4*>(out + (b * C + c) * int64_t(Rp) + rs) = *reinterpret_cast<const uint4*>(t);
   }
 }
 
@@ -1415,17 +1374,18 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
   float* Chat = cv.take<float>(size_t(p) * n1 * n4);
   uint8_t* A8 = cv.take<uint8_t>(size_t(p) * n1 * Kp);
   uint8_t* B8 = cv.take<uint8_t>(size_t(p) * n4 * Kp);
+  uint8_t* B8r = cv.take<uint8_t>(size_t(p) * n2 * n4);   // W(B) codes in row order
   unsigned* amax = cv.take<unsigned>(2 * size_t(p));
   float* inv = cv.take<float>(2 * size_t(p));
   if (!cv.ok) return WP_ERR_WORKSPACE;
   WP_CUDA_TRY(cudaMemsetAsync(amax, 0, 2 * size_t(p) * sizeof(unsigned), st));
   const Fp8Operand da{A, A8, amax, inv, int(n1), int(n2), int(Kp)};
-  const Fp8Operand db{B, nullptr, amax + p, inv + p, int(n2), int(n4), 0};
+  const Fp8Operand db{B, B8r, amax + p, inv + p, int(n2), int(n4), int(n4)};
+  // both operands' rows must allow the vector width (A rows n2, B rows n4)
+  const int vec = fp8_vec<L>(n2 % 4 == 0 && n4 % 4 == 0 && aligned16(A) && aligned16(B),
+                             n2 % 2 == 0 && n4 % 2 == 0);
   {
     // one CTA row per tube group and operand; about 8 CTAs per SM in all
-    // both operands' rows must allow the vector width (A rows n2, B rows n4)
-    const int vec = fp8_vec<L>(n2 % 4 == 0 && n4 % 4 == 0 && aligned16(A) && aligned16(B),
-                               n2 % 2 == 0 && n4 % 2 == 0);
     const int64_t maxx = (std::max(n1 * n2, n2 * n4) / vec + 255) / 256;
     const int64_t bx = std::max<int64_t>(1, std::min<int64_t>(maxx, (int64_t(sm_count()) * 8 + 2 * m - 1) / (2 * m)));
     const dim3 grid{unsigned(bx), unsigned(2 * m), 1u};
@@ -1445,32 +1405,24 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
     WP_TRY(launch_status());
   }
   {
-    const int vec = fp8_vec<L>(n2 % 4 == 0 && aligned16(A), n2 % 2 == 0);
-    const int64_t total = m * (n1 * n2 / vec);
+    // W(A) straight to K-major codes, W(B) to row-order codes (transposed next)
+    const int64_t total = m * ((n1 * n2 + n2 * n4) / vec);
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8));
     WP_PROFILE("lift_quant_fp8", st);
     if constexpr (L <= 3) {
-      if (vec == 4) lift_quant_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(da, p);
+      if (vec == 4) lift_quant_rows_kernel<L, 4><<<unsigned(blocks), 256, 0, st>>>(da, db, p);
     }
     if constexpr (L <= 4) {
-      if (vec == 2) lift_quant_rows_kernel<L, 2><<<unsigned(blocks), 256, 0, st>>>(da, p);
+      if (vec == 2) lift_quant_rows_kernel<L, 2><<<unsigned(blocks), 256, 0, st>>>(da, db, p);
     }
-    if (vec == 1) lift_quant_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(da, p);
+    if (vec == 1) lift_quant_rows_kernel<L, 1><<<unsigned(blocks), 256, 0, st>>>(da, db, p);
     WP_TRY(launch_status());
   }
   {
-    constexpr int TR = QuantTile<L>::TR, CW = QuantTile<L>::CW;
-    constexpr size_t smem = QuantTile<L>::SMEM;
-    static bool attr = false;
-    if (!attr) {
-      WP_CUDA_TRY(cudaFuncSetAttribute(lift_quant_transpose_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem)));
-      attr = true;
-    }
-    const dim3 grid{unsigned((n4 + CW - 1) / CW), unsigned((Kp + TR - 1) / TR), unsigned(m)};
-    WP_PROFILE("lift_quant_transpose_fp8", st);
-    const int vec4 = (n4 % 4 == 0) && aligned16(B);
-    lift_quant_transpose_kernel<L><<<grid, 256, smem, st>>>(B, B8, inv + p, int(n2), int(n4), int(Kp), vec4);
+    const dim3 grid{unsigned((n4 + 63) / 64), unsigned((Kp + 63) / 64), unsigned(p)};
+    const int vec16 = (n4 % 16 == 0);
+    WP_PROFILE("transpose_fp8", st);
+    transpose_bytes_kernel<<<grid, 256, 0, st>>>(B8r, B8, int(n2), int(n4), int(Kp), vec16);
     WP_TRY(launch_status());
   }
   CUtensorMap ma, mb;
