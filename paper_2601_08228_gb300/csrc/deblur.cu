@@ -16,18 +16,30 @@
 
 namespace wp {
 
-// R = C - Y; loss += sum(R^2) + lam * sum(X^2)  (FP64 accumulation of the loss)
+// R = C - Y; with LOSS also loss += sum(R^2) + lam * sum(X^2).  Each thread
+// sums its terms in FP32 with Kahan compensation and the threads' sums are
+// combined in FP64: GB300's FP64 pipe is a small fraction of its FP32 rate,
+// and FP64 arithmetic per element made this pass four times slower than
+// its memory traffic.  Relative error of the loss: a few FP32 roundings.
+template <bool LOSS>
 __global__ void __launch_bounds__(256) residual_loss_kernel(const float* __restrict__ C, const float* __restrict__ Y,
                                                             const float* __restrict__ X, float* __restrict__ R,
                                                             int64_t n, float lam, double* loss) {
-  double acc = 0.0;
+  float sum = 0.f, comp = 0.f;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const float r = C[i] - Y[i];
     R[i] = r;
-    const float x = X[i];
-    acc += double(r) * r + double(lam) * double(x) * x;
+    if constexpr (LOSS) {
+      const float x = X[i];
+      const float term = fmaf(lam * x, x, r * r);
+      const float yk = term - comp;
+      const float t = sum + yk;
+      comp = (t - sum) - yk;
+      sum = t;
+    }
   }
-  if (loss) {
+  if constexpr (LOSS) {
+    double acc = double(sum) - double(comp);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     __shared__ double wsum[8];
@@ -103,7 +115,8 @@ extern "C" int wp_deblur_step(const float* K, const float* Y, float* X, int64_t 
   WP_TRY(wp_wprod(K, X, C, n1, n1, n2, p, L, 0, 0, prec, inner, prod_ws, stream));
   {
     WP_PROFILE("deblur_residual", st);
-    residual_loss_kernel<<<grid_elems(n), 256, 0, st>>>(C, Y, X, R, n, lam, loss);
+    if (loss) residual_loss_kernel<true><<<grid_elems(n), 256, 0, st>>>(C, Y, X, R, n, lam, loss);
+    else residual_loss_kernel<false><<<grid_elems(n), 256, 0, st>>>(C, Y, X, R, n, lam, nullptr);
     WP_TRY(launch_status());
   }
   // dX = K^T *w R by the adjoint backward of the w-product (second operand)

@@ -94,6 +94,51 @@ __global__ void __launch_bounds__(256) split_transpose_kernel(const float* __res
   }
 }
 
+// The same for C % 4 == 0 and a 16-byte aligned input: 64 x 64 tiles, four
+// 16-byte loads per thread in flight, and every thread stores 8 consecutive
+// K-elements of one output row as one 16-byte vector per BF16 copy (the 32
+// lanes of a warp on 32 output rows: conflict-free shared-memory reads).
+// Rp must be a multiple of 8.
+__global__ void __launch_bounds__(256) split_transpose4_kernel(const float* __restrict__ in,
+                                                               __nv_bfloat16* __restrict__ hi,
+                                                               __nv_bfloat16* __restrict__ lo, int R, int C,
+                                                               int Rp) {
+  constexpr int T = 64, LD = T + 1;
+  __shared__ float tile[T * LD];
+  const int c0 = blockIdx.x * T, r0 = blockIdx.y * T;
+  const int64_t b = blockIdx.z;
+  const float* src = in + b * R * int64_t(C);
+  const int tid = threadIdx.x;
+  float4 v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = (tid >> 4) + 16 * k, j = (tid & 15) * 4;
+    const int r = r0 + i, c = c0 + j;
+    v[k] = (r < R && c < C) ? __ldg(reinterpret_cast<const float4*>(src + int64_t(r) * C + c))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float* d = tile + ((tid >> 4) + 16 * k) * LD + (tid & 15) * 4;
+    d[0] = v[k].x; d[1] = v[k].y; d[2] = v[k].z; d[3] = v[k].w;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int w = tid + 256 * k;
+    const int cc = w & 63, chunk = w >> 6;
+    const int c = c0 + cc, rs = r0 + chunk * 8;
+    if (c < C && rs < Rp) {
+      __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) split_bf16(tile[(chunk * 8 + q) * LD + cc], h[q], l[q]);
+      const int64_t o = (b * C + c) * int64_t(Rp) + rs;
+      *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+      if (lo) *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
+    }
+  }
+}
+
 // ---- FP8 operand preparation ------------------------------------------------------------
 
 // amax_bits[b] = max |X[b]| (as the bit pattern of a non-negative float, so
@@ -1076,6 +1121,12 @@ static int split_operand(const float* X, int64_t rows, int64_t K, int64_t Kp, in
     return launch_status();
   }
   // stored (p, K, rows): transpose to (p, rows, Kp)
+  if (rows % 4 == 0 && aligned16(X) && Kp % 8 == 0 && p <= 65535) {
+    const dim3 grid{unsigned((rows + 63) / 64), unsigned((Kp + 63) / 64), unsigned(p)};
+    WP_PROFILE("split_transpose_bf16", st);
+    split_transpose4_kernel<<<grid, 256, 0, st>>>(X, hi, lo, int(K), int(rows), int(Kp));
+    return launch_status();
+  }
   const dim3 grid{unsigned((rows + 31) / 32), unsigned((Kp + 31) / 32), unsigned(std::min<int64_t>(p, 65535))};
   WP_PROFILE("split_transpose_bf16", st);
   split_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(X, hi, lo, int(K), int(rows), int(Kp), int(p));
