@@ -46,29 +46,64 @@ struct LiftDesc {
   int64_t first_block;   // first CTA-chunk index of this tensor
   int32_t plane, p, L, op;
   int32_t chunks_per_group;
+  int32_t vec;           // plane elements per thread (batched_lift_vec)
 };
+
+// Plane elements per thread of the grouped lift: vectors where the plane
+// and both pointers allow, narrower as the group grows so that no case of
+// the one grouped kernel needs more than 32 live values per thread.
+__host__ __device__ constexpr int batched_lift_vec_max(int L) { return L <= 2 ? 4 : (L == 3 ? 2 : 1); }
 
 constexpr int BL_THREADS = 256;
 
 // ---- phase 1 / 4: grouped lifting ---------------------------------------------------
 
-template <int L>
+// The wavelet-domain copies of the items never leave the batched launch, so
+// they use the group-interleaved slice order (local index t of group g at
+// slice g * 2^L + t): both directions stream 2^L consecutive slices.
+template <int L, int VEC>
 __device__ __forceinline__ void lift_chunk(const LiftDesc& d, int64_t g, int64_t e) {
   constexpr int G = 1 << L;
-  float x[G], y[G];
   const bool fwd = (d.op == LIFT_FWD);
+  float v[G][VEC];
 #pragma unroll
   for (int t = 0; t < G; ++t) {
-    const int64_t slice = fwd ? g * G + t : mallat_slice<L>(t, g, d.p);
-    x[t] = __ldg(d.src + slice * d.plane + e);
+    const float* src = d.src + (g * G + t) * d.plane + e;
+    if constexpr (VEC == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+      v[t][0] = q.x; v[t][1] = q.y; v[t][2] = q.z; v[t][3] = q.w;
+    } else if constexpr (VEC == 2) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(src));
+      v[t][0] = q.x; v[t][1] = q.y;
+    } else {
+      v[t][0] = __ldg(src);
+    }
   }
-  if (fwd) lift_group<L>(x, y);
-  else ilift_group<L>(x, y);
+#pragma unroll
+  for (int j = 0; j < VEC; ++j) {
+    float x[G], y[G];
+#pragma unroll
+    for (int t = 0; t < G; ++t) x[t] = v[t][j];
+    if (fwd) lift_group<L>(x, y);
+    else ilift_group<L>(x, y);
+#pragma unroll
+    for (int t = 0; t < G; ++t) v[t][j] = y[t];
+  }
 #pragma unroll
   for (int t = 0; t < G; ++t) {
-    const int64_t slice = fwd ? mallat_slice<L>(t, g, d.p) : g * G + t;
-    d.dst[slice * d.plane + e] = y[t];
+    float* dst = d.dst + (g * G + t) * d.plane + e;
+    if constexpr (VEC == 4) *reinterpret_cast<float4*>(dst) = make_float4(v[t][0], v[t][1], v[t][2], v[t][3]);
+    else if constexpr (VEC == 2) *reinterpret_cast<float2*>(dst) = make_float2(v[t][0], v[t][1]);
+    else *dst = v[t][0];
   }
+}
+
+template <int L>
+__device__ __forceinline__ void lift_chunk_vec(const LiftDesc& d, int64_t g, int64_t e) {
+  constexpr int VM = batched_lift_vec_max(L);
+  if (VM >= 4 && d.vec == 4) lift_chunk<L, VM >= 4 ? 4 : 1>(d, g, e);
+  else if (VM >= 2 && d.vec == 2) lift_chunk<L, VM >= 2 ? 2 : 1>(d, g, e);
+  else lift_chunk<L, 1>(d, g, e);
 }
 
 __global__ void __launch_bounds__(BL_THREADS) batched_lift_kernel(const LiftDesc* __restrict__ descs, int ndesc,
@@ -84,15 +119,15 @@ __global__ void __launch_bounds__(BL_THREADS) batched_lift_kernel(const LiftDesc
     const LiftDesc d = descs[lo];
     const int64_t local = b - d.first_block;
     const int64_t g = local / d.chunks_per_group;
-    const int64_t e = (local % d.chunks_per_group) * BL_THREADS + threadIdx.x;
+    const int64_t e = ((local % d.chunks_per_group) * BL_THREADS + threadIdx.x) * d.vec;
     if (e >= d.plane) continue;
     switch (d.L) {
-      case 0: lift_chunk<0>(d, g, e); break;
-      case 1: lift_chunk<1>(d, g, e); break;
-      case 2: lift_chunk<2>(d, g, e); break;
-      case 3: lift_chunk<3>(d, g, e); break;
-      case 4: lift_chunk<4>(d, g, e); break;
-      default: lift_chunk<5>(d, g, e); break;
+      case 0: lift_chunk_vec<0>(d, g, e); break;
+      case 1: lift_chunk_vec<1>(d, g, e); break;
+      case 2: lift_chunk_vec<2>(d, g, e); break;
+      case 3: lift_chunk_vec<3>(d, g, e); break;
+      case 4: lift_chunk_vec<4>(d, g, e); break;
+      default: lift_chunk_vec<5>(d, g, e); break;
     }
   }
 }
@@ -272,7 +307,12 @@ static int64_t make_lift_descs(std::vector<LiftDesc>& d, const float* src, float
   x.p = p;
   x.L = L;
   x.op = op;
-  x.chunks_per_group = (plane + BL_THREADS - 1) / BL_THREADS;
+  // vectors need a plane of whole vectors and 16- (8-) byte aligned tensors
+  const int vm = batched_lift_vec_max(L);
+  const bool a16 = aligned16(src) && aligned16(dst);
+  const bool a8 = (reinterpret_cast<uintptr_t>(src) & 7u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 7u) == 0;
+  x.vec = (vm >= 4 && plane % 4 == 0 && a16) ? 4 : (vm >= 2 && plane % 2 == 0 && a8) ? 2 : 1;
+  x.chunks_per_group = (plane + BL_THREADS * x.vec - 1) / (BL_THREADS * x.vec);
   d.push_back(x);
   return first + int64_t(p >> L) * x.chunks_per_group;
 }
