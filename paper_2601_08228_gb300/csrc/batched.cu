@@ -136,10 +136,15 @@ __global__ void __launch_bounds__(BL_THREADS) batched_lift_kernel(const LiftDesc
 
 constexpr int BMAX = 64;
 
+// One wavelet-domain slice per CTA iteration: A_hat_k staged transposed and
+// B_hat_k as is in shared memory (rows of BS floats, 16-byte aligned), then
+// 4 x 4 output micro-tiles per thread: two 16-byte shared loads per 16 FMAs.
+constexpr int BS = BMAX + 4;
+
 __global__ void batched_facewise_kernel(const BItem* __restrict__ items, const int2* __restrict__ units,
                                         int64_t nunits) {
-  __shared__ float As[BMAX][BMAX + 1];
-  __shared__ float Bs[BMAX][BMAX + 1];
+  __shared__ __align__(16) float At[BMAX * BS];   // At[k][i] = A_hat_k[i][k]
+  __shared__ __align__(16) float Bs[BMAX * BS];   // Bs[k][j] = B_hat_k[k][j]
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int2 uk = units[u];
     const BItem it = items[uk.x];
@@ -147,14 +152,38 @@ __global__ void batched_facewise_kernel(const BItem* __restrict__ items, const i
     const float* a = it.Ah + int64_t(uk.y) * n1 * n2;
     const float* bm = it.Bh + int64_t(uk.y) * n2 * n4;
     float* c = it.Ch + int64_t(uk.y) * n1 * n4;
-    for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) As[i / n2][i % n2] = a[i];
-    for (int i = threadIdx.x; i < n2 * n4; i += blockDim.x) Bs[i / n4][i % n4] = bm[i];
+    for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) {
+      const int row = i / n2, col = i - row * n2;
+      At[col * BS + row] = __ldg(a + i);
+    }
+    for (int i = threadIdx.x; i < n2 * n4; i += blockDim.x) {
+      const int row = i / n4, col = i - row * n4;
+      Bs[row * BS + col] = __ldg(bm + i);
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < n1 * n4; i += blockDim.x) {
-      const int row = i / n4, col = i % n4;
-      float acc = 0.f;
-      for (int k = 0; k < n2; ++k) acc = fmaf(As[row][k], Bs[k][col], acc);
-      c[i] = acc;
+    // micro-tile (ti, tj): rows 4 ti .. 4 ti + 3, columns 4 tj .. 4 tj + 3
+    const int mt = (n1 + 3) >> 2, nt = (n4 + 3) >> 2;
+    for (int w = threadIdx.x; w < mt * nt; w += blockDim.x) {
+      const int ti = w / nt, tj = w - ti * nt;
+      float acc[4][4] = {};
+      for (int k = 0; k < n2; ++k) {
+        const float4 av = *reinterpret_cast<const float4*>(At + k * BS + 4 * ti);
+        const float4 bv = *reinterpret_cast<const float4*>(Bs + k * BS + 4 * tj);
+        const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(ar[x], br[y], acc[x][y]);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const int row = 4 * ti + x;
+        if (row < n1) {
+#pragma unroll
+          for (int y = 0; y < 4; ++y)
+            if (4 * tj + y < n4) c[row * n4 + 4 * tj + y] = acc[x][y];
+        }
+      }
     }
     __syncthreads();
   }
