@@ -304,6 +304,14 @@ def run_ours(args):
     for _ in range(args.warmup):
         flush.zero_()
         step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    # one untimed step with every launch bracketed by events: the per-kernel
+    # breakdown and the dominant kernel
+    capi.wp_profile_begin()
+    flush.zero_()
+    step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    torch.cuda.synchronize()
+    prof_step = capi.wp_profile_end()
+    dominant = max(prof_step.items(), key=lambda kv: kv[1][1])[0]
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -311,6 +319,9 @@ def run_ours(args):
     launches0 = capi.wp_launch_count()
     capi.wp_jacobi_stats()          # clear the sweep counters
     with ClockSampler(local) as clk:
+        # timed region: events around the dominant kernel's launches only, so
+        # that they do not separate the other kernels of the step
+        capi.wp_profile_only(dominant)
         capi.wp_profile_begin()
         torch.cuda.synchronize()
         for i in range(args.steps):
@@ -318,6 +329,7 @@ def run_ours(args):
             step(events[i])
         torch.cuda.synchronize()
         prof = capi.wp_profile_end()
+        capi.wp_profile_only(None)
     launches = capi.wp_launch_count() - launches0
     tot_sw, max_sw = capi.wp_jacobi_stats()
     jac = {"total_sweeps": tot_sw, "max_sweeps": max_sw}
@@ -362,7 +374,7 @@ def run_ours(args):
         "fp32_tflops": args.steps * wprod_flops() / fp32 / 1e12,
         "rel_err": {"mixed": err_mixed, "fp32": err_fp32},
         "roofline": roof,
-        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+        "kernels_ms_per_step": {k: v[1] for k, v in prof_step.items()},
         "jacobi_sweeps": jac,
         "clocks": clocks,
         "e2e": e2e,

@@ -96,8 +96,13 @@ WP_API uint64_t wp_launch_count(void);
  * synchronises the device and totals the elapsed times per kernel name;
  * wp_profile_count() / wp_profile_get() read the totals (name copied into
  * `name`, NUL-terminated, at most name_len bytes).  Do not enable it while a
- * stream is being captured into a CUDA graph. */
+ * stream is being captured into a CUDA graph.  wp_profile_only(name) limits
+ * the recording to launches of that kernel name (NULL or "": every launch),
+ * so that the events do not separate the other launches of a timed region
+ * (a recorded event between two kernels ends the overlap that programmatic
+ * stream serialisation gives them). */
 WP_API int wp_profile_begin(void);
+WP_API int wp_profile_only(const char* name);
 WP_API int wp_profile_end(void);
 WP_API int wp_profile_count(void);
 WP_API int wp_profile_get(int index, char* name, int name_len, int64_t* launches,

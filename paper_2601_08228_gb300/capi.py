@@ -59,6 +59,7 @@ _SIGNATURES = {
     "wp_get_device_error": ([_P], _I),
     "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
     "wp_profile_begin": ([], _I),
+    "wp_profile_only": ([ctypes.c_char_p], _I),
     "wp_profile_end": ([], _I),
     "wp_profile_count": ([], _I),
     "wp_profile_get": ([_I, ctypes.c_char_p, _I, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)], _I),
@@ -359,6 +360,11 @@ class BatchedLaunch:
 
     def run(self):
         _check(lib().wp_batched_run(ctypes.byref(self.plan), _ptr(self.ws), _stream()), "wp_batched_run")
+
+
+def wp_profile_only(name=None):
+    """Limit per-kernel timing to launches named `name` (None: all launches)."""
+    _check(lib().wp_profile_only(name.encode() if name else None), "wp_profile_only")
 
 
 def wp_profile_begin():

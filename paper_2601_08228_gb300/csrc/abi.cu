@@ -21,6 +21,7 @@ struct ProfRecord { const char* name; cudaEvent_t start, stop; };
 struct ProfTotal { std::string name; long launches; double ms; };
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
+static std::string g_prof_only;   // record only launches of this name (empty: all)
 static std::vector<ProfRecord> g_prof_records;
 static std::vector<cudaEvent_t> g_prof_pool;
 static std::vector<ProfTotal> g_prof_totals;
@@ -38,8 +39,9 @@ static cudaEvent_t prof_event() {
   return e;
 }
 
-void profile_record(const char*, cudaStream_t st, cudaEvent_t* start, cudaEvent_t* stop) {
+void profile_record(const char* name, cudaStream_t st, cudaEvent_t* start, cudaEvent_t* stop) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_only.empty() && g_prof_only != name) return;
   *start = prof_event();
   *stop = prof_event();
   if (*start) cudaEventRecord(*start, st);
@@ -120,6 +122,12 @@ extern "C" int wp_profile_begin(void) {
   wp::g_prof_records.clear();
   wp::g_prof_totals.clear();
   wp::g_prof_on = true;
+  return WP_OK;
+}
+
+extern "C" int wp_profile_only(const char* name) {
+  std::lock_guard<std::mutex> lk(wp::g_prof_mu);
+  wp::g_prof_only = name ? name : "";
   return WP_OK;
 }
 
