@@ -107,8 +107,12 @@ def test_wprod_bf16x3_full_size_sampled():
     assert O.rel_fro(C[:, rows][:, :, cols], ref) <= TOL_X3
 
 
-def test_backward_bf16x3_parity():
-    p, n1, n2, n4, L = 32, 48, 80, 40, 4
+@pytest.mark.parametrize("p,n1,n2,n4,L", [
+    (32, 48, 80, 40, 4),        # transposing splits in 64-tiles (rows multiple of 4)
+    (24, 33, 17, 45, 3),        # odd rows: the 32-tile fallback transposes
+    (64, 24, 36, 20, 5),        # L = 5: group-interleaved cotangents
+])
+def test_backward_bf16x3_parity(p, n1, n2, n4, L):
     A, B, G = rand((p, n1, n2), 7), rand((p, n2, n4), 8), rand((p, n1, n4), 9)
     dA, dB = capi.wp_wprod_backward(dev(A), dev(B), dev(G), L, prec="bf16x3")
     rA, rB = O.wprod_grad(A, B, G, L)
