@@ -552,6 +552,25 @@ def _extras(capi, args):
     out["deblur_512x512x128"] = {"ms_per_step": step, "ms_200_steps": 200 * step,
                                  "tflops": 2 * 2 * n ** 3 * p / (step / 1e3) / 1e12, "prec": "bf16x3"}
     del Kd, Yd, X, ws
+    # wpinv of 192 slices of 256 x 192, iid N(0, 1) (wavelet slices with
+    # condition numbers near 14), L = 3, one refinement step.  The HSI cube
+    # itself is no pinv workload in FP32: its s_L slices reach condition
+    # numbers of 1e7 and the cut-off falls inside a dense part of the spectrum.
+    A_h = np.random.default_rng(4).standard_normal((192, 256, 192)).astype(np.float32)
+    Ad = torch.from_numpy(A_h).cuda()
+    wsp = torch.empty(capi.wp_wpinv_workspace(256, 192, 192, 3), dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        X = capi.wp_wpinv(Ad, 3, refine_iters=1, ws=wsp)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(5):
+        X = capi.wp_wpinv(Ad, 3, refine_iters=1, ws=wsp)
+    b.record()
+    torch.cuda.synchronize()
+    t_pinv = a.elapsed_time(b) / 5
+    err_pinv = O.rel_fro(X.cpu().numpy(), O.wpinv(A_h, 3))
+    out["wpinv_256x192x192_L3"] = {"ms": t_pinv, "refine_iters": 1, "rel_err": err_pinv}
+    del Ad, X, wsp
     # precision study: A 1024x1024x256 by B 1024x512x256, per-slice 10^U[-3,3] scales, L = 4
     A, B = synth.scaled_pair(1024, 1024, 512, 256, seed=0)
     ref = O.wprod(A, B, 4)

@@ -267,7 +267,9 @@ WP_API int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V, int
 /* X = A^dagger for A (p, m, n); X is (p, n, m).  Per wavelet slice
  * pinv = V Sigma^+ U^T from the Jacobi SVD, keeping sigma_i > rtol sigma_max
  * (rtol < 0 selects max(m, n) * FLT_EPSILON), then `refine_iters` steps of
- * X <- X + X (I - A X) evaluated with FP64 residual accumulation, then W^{-1}. */
+ * X <- X + X (I - A X) with the residual I - A X evaluated as compensated
+ * dot products (twice working precision, Dot2 of Ogita, Rump and Oishi), then
+ * W^{-1}. */
 WP_API int wp_wpinv_workspace(int64_t m, int64_t n, int64_t p, int L, size_t* bytes);
 WP_API int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t p, int L, double rtol,
              int refine_iters, void* ws, size_t ws_bytes, void* stream);

@@ -320,6 +320,13 @@ def wp_wsvd(A, L, r, sparse=False, factors=False, factors_in_wavelet_domain=True
 
 # ---- Moore-Penrose inverse ----------------------------------------------------------
 
+def wp_wpinv_workspace(m, n, p, L):
+    """Workspace bytes of wp_wpinv for A (p, m, n)."""
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_wpinv_workspace(m, n, p, L, ctypes.byref(nbytes)), "wp_wpinv_workspace")
+    return nbytes.value
+
+
 def wp_wpinv(A, L, rtol=-1.0, refine_iters=0, ws=None):
     _req(A, "A")
     p, m, n = A.shape

@@ -13,7 +13,8 @@
 //          n1 >= n2:  X_hat_k = (A_k^T U) diag(w) U^T   (V = A^T U Sigma^-1)
 //          n1 <  n2:  X_hat_k = V diag(w) (A_k V)^T      (U = A V Sigma^-1)
 //          then optional refinement X <- X + X (I - A X) with the residual
-//          accumulated in FP64, and X = W^{-1}(X_hat).
+//          in compensated (twice working precision) arithmetic, and
+//          X = W^{-1}(X_hat).
 
 #include "common.cuh"
 #include "internal.cuh"
@@ -79,18 +80,38 @@ __global__ void __launch_bounds__(256) pinv_scale_kernel(float* __restrict__ T, 
   }
 }
 
-// R = I - A X per slice with FP64 accumulation (A: m x n, X: n x m).
-__global__ void __launch_bounds__(256) residual_f64_kernel(const float* __restrict__ A, const float* __restrict__ X,
-                                                           float* __restrict__ R, int m, int n, int batch) {
+// R = I - A X per slice (A: m x n, X: n x m), each entry a compensated dot
+// product: the algorithm Dot2 of Ogita, Rump and Oishi ("Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005), as accurate as if computed
+// in twice the working precision and then rounded.  Every product a x is
+// split exactly into p + e with one FMA (e = fma(a, x, -p)), the p are
+// added with TwoSum (s + t = hi + p exactly), and the rounding errors e and
+// t are summed plainly into `lo`.  With X close to the pseudo-inverse,
+// A X is I + E with E of order kappa * eps, so R needs the extra precision;
+// GB300 runs FP32 arithmetic at many times its FP64 rate.  The diagonal
+// 1 - hi is exact (Sterbenz: hi is within a factor 2 of 1), so R rounds once.
+__global__ void __launch_bounds__(256) residual_dot2_kernel(const float* __restrict__ A, const float* __restrict__ X,
+                                                            float* __restrict__ R, int m, int n, int batch) {
   const int64_t total = int64_t(batch) * m * m;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t s = i / (int64_t(m) * m);
     const int rem = int(i - s * m * m), row = rem / m, col = rem % m;
     const float* a = A + (s * m + row) * n;
     const float* x = X + s * int64_t(n) * m + col;
-    double acc = 0.0;
-    for (int l = 0; l < n; ++l) acc = fma(double(a[l]), double(x[int64_t(l) * m]), acc);
-    R[i] = float((row == col ? 1.0 : 0.0) - acc);
+    float hi = 0.f, lo = 0.f;
+    for (int l = 0; l < n; ++l) {
+      const float av = __ldg(a + l), xv = __ldg(x + int64_t(l) * m);
+      // _rn intrinsics: never contracted into FMAs, so every step rounds as written
+      const float pr = __fmul_rn(av, xv);
+      const float pe = fmaf(av, xv, -pr);          // av * xv = pr + pe exactly
+      const float sm = __fadd_rn(hi, pr);          // TwoSum(hi, pr) = sm + se exactly
+      const float bb = __fsub_rn(sm, hi);
+      const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bb)), __fsub_rn(pr, bb));
+      hi = sm;
+      lo = __fadd_rn(lo, __fadd_rn(pe, se));
+    }
+    const float d = (row == col) ? 1.f - hi : -hi;
+    R[i] = d - lo;
   }
 }
 
@@ -283,8 +304,8 @@ extern "C" int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t 
   }
   for (int it = 0; it < refine_iters; ++it) {
     {
-      WP_PROFILE("pinv_residual_f64", st);
-      residual_f64_kernel<<<grid_for(p * m * m), 256, 0, st>>>(Ah, Xh, R, M, N, P);
+      WP_PROFILE("pinv_residual", st);
+      residual_dot2_kernel<<<grid_for(p * m * m), 256, 0, st>>>(Ah, Xh, R, M, N, P);
       WP_TRY(launch_status());
     }
     WP_TRY(sgemm_batched(Xh, R, XR, N, M, M, false, false, P, st));
