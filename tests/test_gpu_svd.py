@@ -176,7 +176,7 @@ def _kappa(A, L):
 def test_wpinv_parity_and_penrose(p, m, n, L, refine):
     """Without refinement an FP32 pseudo-inverse is accurate to ~kappa eps
     (kappa: worst wavelet-slice condition number) and its Penrose residuals
-    to ~kappa^2 eps; the FP64-residual refinement brings X to the 1e-4 bar and
+    to ~kappa^2 eps; the refinement (compensated residuals) brings X to the 1e-4 bar and
     the residuals to ~kappa eps (the FP32 representation limit of X)."""
     A = rand((p, m, n), m * n + p)
     X = host(capi.wp_wpinv(dev(A), L, refine_iters=refine))
