@@ -90,28 +90,49 @@ __global__ void __launch_bounds__(256) pinv_scale_kernel(float* __restrict__ T, 
 // A X is I + E with E of order kappa * eps, so R needs the extra precision;
 // GB300 runs FP32 arithmetic at many times its FP64 rate.  The diagonal
 // 1 - hi is exact (Sterbenz: hi is within a factor 2 of 1), so R rounds once.
+// Every thread takes RB consecutive rows of one column of R, so each loaded
+// element of X serves RB dot products (the rows of A are broadcast loads
+// shared by the warp's lanes).
+constexpr int RES_RB = 8;
+
 __global__ void __launch_bounds__(256) residual_dot2_kernel(const float* __restrict__ A, const float* __restrict__ X,
                                                             float* __restrict__ R, int m, int n, int batch) {
-  const int64_t total = int64_t(batch) * m * m;
+  const int mb = (m + RES_RB - 1) / RES_RB;
+  const int64_t total = int64_t(batch) * mb * m;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t s = i / (int64_t(m) * m);
-    const int rem = int(i - s * m * m), row = rem / m, col = rem % m;
-    const float* a = A + (s * m + row) * n;
+    const int64_t s = i / (int64_t(mb) * m);
+    const int rem = int(i - s * mb * m), rb = rem / m, col = rem % m;
+    const int row0 = rb * RES_RB;
+    const float* a = A + (s * m + row0) * n;
     const float* x = X + s * int64_t(n) * m + col;
-    float hi = 0.f, lo = 0.f;
+    float hi[RES_RB], lo[RES_RB];
+#pragma unroll
+    for (int q = 0; q < RES_RB; ++q) hi[q] = lo[q] = 0.f;
     for (int l = 0; l < n; ++l) {
-      const float av = __ldg(a + l), xv = __ldg(x + int64_t(l) * m);
-      // _rn intrinsics: never contracted into FMAs, so every step rounds as written
-      const float pr = __fmul_rn(av, xv);
-      const float pe = fmaf(av, xv, -pr);          // av * xv = pr + pe exactly
-      const float sm = __fadd_rn(hi, pr);          // TwoSum(hi, pr) = sm + se exactly
-      const float bb = __fsub_rn(sm, hi);
-      const float se = __fadd_rn(__fsub_rn(hi, __fsub_rn(sm, bb)), __fsub_rn(pr, bb));
-      hi = sm;
-      lo = __fadd_rn(lo, __fadd_rn(pe, se));
+      const float xv = __ldg(x + int64_t(l) * m);
+#pragma unroll
+      for (int q = 0; q < RES_RB; ++q) {
+        if (row0 + q < m) {
+          const float av = __ldg(a + int64_t(q) * n + l);
+          // _rn intrinsics: never contracted into FMAs, so every step rounds as written
+          const float pr = __fmul_rn(av, xv);
+          const float pe = fmaf(av, xv, -pr);          // av * xv = pr + pe exactly
+          const float sm = __fadd_rn(hi[q], pr);       // TwoSum(hi, pr) = sm + se exactly
+          const float bb = __fsub_rn(sm, hi[q]);
+          const float se = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(sm, bb)), __fsub_rn(pr, bb));
+          hi[q] = sm;
+          lo[q] = __fadd_rn(lo[q], __fadd_rn(pe, se));
+        }
+      }
     }
-    const float d = (row == col) ? 1.f - hi : -hi;
-    R[i] = d - lo;
+#pragma unroll
+    for (int q = 0; q < RES_RB; ++q) {
+      const int row = row0 + q;
+      if (row < m) {
+        const float d = (row == col) ? 1.f - hi[q] : -hi[q];
+        R[(s * m + row) * int64_t(m) + col] = d - lo[q];
+      }
+    }
   }
 }
 
@@ -305,7 +326,7 @@ extern "C" int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t 
   for (int it = 0; it < refine_iters; ++it) {
     {
       WP_PROFILE("pinv_residual", st);
-      residual_dot2_kernel<<<grid_for(p * m * m), 256, 0, st>>>(Ah, Xh, R, M, N, P);
+      residual_dot2_kernel<<<grid_for(p * ((m + RES_RB - 1) / RES_RB) * m), 256, 0, st>>>(Ah, Xh, R, M, N, P);
       WP_TRY(launch_status());
     }
     WP_TRY(sgemm_batched(Xh, R, XR, N, M, M, false, false, P, st));
