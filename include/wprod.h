@@ -295,7 +295,8 @@ typedef struct {
   int32_t gemm_threads, svd_threads;   /* CTA sizes (autotuned when tune = 1) */
   int32_t svd_vec_floats;              /* max over items of max(n1, n2) * r */
   int64_t n_units;                     /* wavelet-domain slices over all items */
-  int64_t n_units_narrow;              /* the first n_units_narrow of them have min(n1, n2) <= 32 */
+  int64_t n_units_narrow;              /* the first n_units_narrow of them have min(n1, n2) <= 32, */
+  int64_t n_units_mid;                 /* the next n_units_mid 32 < min(n1, n2) <= 48 */
   int64_t lift_fwd_blocks, lift_inv_blocks;
   uint64_t items_off, lift_fwd_off, lift_inv_off, units_off;
 } wp_batch_plan;

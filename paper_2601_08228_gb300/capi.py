@@ -41,7 +41,7 @@ class WPBatchItem(ctypes.Structure):
 class WPBatchPlan(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("n_lift_fwd", ctypes.c_int32), ("n_lift_inv", ctypes.c_int32),
                 ("gemm_threads", ctypes.c_int32), ("svd_threads", ctypes.c_int32),
-                ("svd_vec_floats", ctypes.c_int32), ("n_units", ctypes.c_int64), ("n_units_narrow", ctypes.c_int64),
+                ("svd_vec_floats", ctypes.c_int32), ("n_units", ctypes.c_int64), ("n_units_narrow", ctypes.c_int64), ("n_units_mid", ctypes.c_int64),
                 ("lift_fwd_blocks", ctypes.c_int64), ("lift_inv_blocks", ctypes.c_int64),
                 ("items_off", ctypes.c_uint64), ("lift_fwd_off", ctypes.c_uint64), ("lift_inv_off", ctypes.c_uint64),
                 ("units_off", ctypes.c_uint64)]

@@ -13,8 +13,8 @@
 //                   slice's columns in registers, jacobi_block.cuh), the
 //                   rank-r slice C_hat_k = U_r U_r^T A_hat_k (or
 //                   A_hat_k V_r V_r^T) rebuilt in the same CTA; slices of at
-//                   most 32 columns on 4-warp CTAs, the rest on CTAs sized
-//                   for 64 columns (two launches)
+//                   most 32 / 48 columns on 4- / 6-warp CTAs, the rest on CTAs
+//                   sized for 64 columns (three launches)
 //   4. inverse lifting of every C_hat and C_hat_r
 // wp_batched_run performs no allocation, host synchronisation or copy, so it
 // can be captured in a CUDA graph.  The CTA sizes of phases 2 and 3 are picked
@@ -393,12 +393,19 @@ static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t 
   return launch_batched_jacobi_t<8, 4>(items, units, n, vec_floats, st);
 }
 
-// Slices with at most 32 columns: 4 warps of 4-column blocks, so that no warp
-// of a CTA idles and twice as many slices run per SM as on 8-warp CTAs.
+// Slices with at most 32 (48) columns: 4 (6) warps of 4-column blocks, so
+// that at most one warp of a CTA idles and more slices run per SM than on
+// 8-warp CTAs.
 static int launch_batched_jacobi_narrow(const BItem* items, const int2* units, int64_t n, int vec_floats,
                                         cudaStream_t st) {
   if (n < 1) return WP_OK;
   return launch_batched_jacobi_t<4, 4>(items, units, n, vec_floats, st);
+}
+
+static int launch_batched_jacobi_mid(const BItem* items, const int2* units, int64_t n, int vec_floats,
+                                     cudaStream_t st) {
+  if (n < 1) return WP_OK;
+  return launch_batched_jacobi_t<4, 6>(items, units, n, vec_floats, st);
 }
 
 // Time one candidate configuration of a phase (median of 3 runs).
@@ -447,7 +454,8 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
   float* data = reinterpret_cast<float*>(base + lay.data_off);
   std::vector<BItem> bi(count);
   std::vector<LiftDesc> l1, l2;
-  std::vector<int2> units, wide;   // narrow slices (min(n1, n2) <= 32) first
+  // narrow slices (min(n1, n2) <= 32) first, then mid (<= 48), then wide
+  std::vector<int2> units, mid, wide;
   units.reserve(size_t(lay.nunits));
   int64_t b1 = 0, b2 = 0;
   for (int i = 0; i < count; ++i) {
@@ -465,9 +473,11 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
     b1 = make_lift_descs(l1, t.B, x.Bh, t.n2 * t.n4, t.p, t.L, LIFT_FWD, b1);
     b2 = make_lift_descs(l2, x.Ch, t.C, t.n1 * t.n4, t.p, t.L, LIFT_INV, b2);
     b2 = make_lift_descs(l2, x.Crh, t.C_r, t.n1 * t.n2, t.p, t.L, LIFT_INV, b2);
-    for (int k = 0; k < t.p; ++k) (std::min(t.n1, t.n2) <= 32 ? units : wide).push_back(make_int2(i, k));
+    const int nv = std::min(t.n1, t.n2);
+    for (int k = 0; k < t.p; ++k) (nv <= 32 ? units : nv <= 48 ? mid : wide).push_back(make_int2(i, k));
   }
-  const int64_t n_narrow = int64_t(units.size());
+  const int64_t n_narrow = int64_t(units.size()), n_mid = int64_t(mid.size());
+  units.insert(units.end(), mid.begin(), mid.end());
   units.insert(units.end(), wide.begin(), wide.end());
   cudaStream_t st = as_stream(stream);
   WP_CUDA_TRY(cudaMemcpyAsync(base + lay.items_off, bi.data(), bi.size() * sizeof(BItem), cudaMemcpyHostToDevice, st));
@@ -486,6 +496,7 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
   plan->lift_inv_blocks = b2;
   plan->n_units = lay.nunits;
   plan->n_units_narrow = n_narrow;
+  plan->n_units_mid = n_mid;
   plan->gemm_threads = 256;
   plan->svd_threads = 128;
   plan->svd_vec_floats = 1;
@@ -505,7 +516,7 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
     best = 1e30f;
     for (int thr : {128, 256}) {
       const float t =
-          time_candidate([&] { launch_batched_jacobi(di, du + n_narrow, lay.nunits - n_narrow, thr,
+          time_candidate([&] { launch_batched_jacobi(di, du + n_narrow + n_mid, lay.nunits - n_narrow - n_mid, thr,
                                                      plan->svd_vec_floats, st); }, st);
       if (t < best) { best = t; plan->svd_threads = thr; }
     }
@@ -518,7 +529,9 @@ extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream)
   if (!plan || !ws) return WP_ERR_NULL;
   if (plan->count < 1 || plan->n_units < 1) return WP_ERR_SHAPE;
   if (plan->svd_vec_floats < 1 || plan->svd_vec_floats > BMAX * BMAX) return WP_ERR_SHAPE;
-  if (plan->n_units_narrow < 0 || plan->n_units_narrow > plan->n_units) return WP_ERR_SHAPE;
+  if (plan->n_units_narrow < 0 || plan->n_units_mid < 0 ||
+      plan->n_units_narrow + plan->n_units_mid > plan->n_units)
+    return WP_ERR_SHAPE;
   char* base = static_cast<char*>(ws);
   cudaStream_t st = as_stream(stream);
   const BItem* di = reinterpret_cast<const BItem*>(base + plan->items_off);
@@ -526,9 +539,11 @@ extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream)
   WP_TRY(launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_fwd_off), plan->n_lift_fwd,
                              plan->lift_fwd_blocks, st));
   WP_TRY(launch_batched_gemm(di, du, plan->n_units, plan->gemm_threads, st));
-  WP_TRY(launch_batched_jacobi_narrow(di, du, plan->n_units_narrow, plan->svd_vec_floats, st));
-  WP_TRY(launch_batched_jacobi(di, du + plan->n_units_narrow, plan->n_units - plan->n_units_narrow,
-                               plan->svd_threads, plan->svd_vec_floats, st));
+  const int64_t nn = plan->n_units_narrow, nm = plan->n_units_mid;
+  WP_TRY(launch_batched_jacobi_narrow(di, du, nn, plan->svd_vec_floats, st));
+  WP_TRY(launch_batched_jacobi_mid(di, du + nn, nm, plan->svd_vec_floats, st));
+  WP_TRY(launch_batched_jacobi(di, du + nn + nm, plan->n_units - nn - nm, plan->svd_threads, plan->svd_vec_floats,
+                               st));
   return launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_inv_off), plan->n_lift_inv,
                              plan->lift_inv_blocks, st);
 }
