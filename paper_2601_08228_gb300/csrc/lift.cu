@@ -78,24 +78,43 @@ __device__ __forceinline__ void store_vec(float* p, const float* v) {
 // Launched with programmatic serialisation: it may start while the previous
 // kernel of the stream finishes and waits for that kernel's completion before
 // reading; it lets its own successor start early the same way.
-template <int L, int VEC, int OP, bool IL>
+//
+// GF (group-fastest): CTA-sized chunks are ordered with the tube group
+// fastest, so the CTAs in flight cover every group at nearby plane offsets
+// instead of every offset of two or three groups.  Used for the ops that
+// gather a group from its Mallat positions at L >= 4, where it streams
+// faster (measured at 256 slices of 1024 x 512: 4.4 against 3.5 TB/s at
+// L = 4, 2.8 against 2.2 TB/s at L = 5).
+template <int L, int VEC, int OP, bool IL, bool GF>
 __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__ in,
                                                        float* __restrict__ out, int64_t plane,
                                                        int64_t p, int64_t nvec, int64_t total) {
   constexpr int G = 1 << L;
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  for (int64_t item = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; item < total;
-       item += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t g = item / nvec;
-    const int64_t e = (item - g * nvec) * VEC;
+  const int64_t m = p >> L;
+  const int64_t nchunk = (nvec + blockDim.x - 1) / blockDim.x;
+  const int64_t nwork = GF ? m * nchunk : total;
+  const int64_t first = GF ? int64_t(blockIdx.x) : int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t stride = GF ? int64_t(gridDim.x) : int64_t(gridDim.x) * blockDim.x;
+  for (int64_t w = first; w < nwork; w += stride) {
+    int64_t g, iv;
+    if constexpr (GF) {
+      g = w % m;
+      iv = (w / m) * blockDim.x + threadIdx.x;
+      if (iv >= nvec) continue;
+    } else {
+      g = w / nvec;
+      iv = w - g * nvec;
+    }
+    const int64_t e = iv * VEC;
     float v[G][VEC];
 #pragma unroll
     for (int t = 0; t < G; ++t) {
       const int64_t slice = (reads_spatial(OP) || IL) ? g * G + t : mallat_slice<L>(t, g, p);
       load_vec<VEC>(in + slice * plane + e, v[t]);
     }
-    float w[G][VEC];
+    float w2[G][VEC];
 #pragma unroll
     for (int c = 0; c < VEC; ++c) {
       float x[G], y[G];
@@ -103,12 +122,12 @@ __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__
       for (int t = 0; t < G; ++t) x[t] = v[t][c];
       group_op<L, OP>(x, y);
 #pragma unroll
-      for (int t = 0; t < G; ++t) w[t][c] = y[t];
+      for (int t = 0; t < G; ++t) w2[t][c] = y[t];
     }
 #pragma unroll
     for (int t = 0; t < G; ++t) {
       const int64_t slice = (reads_spatial(OP) && !IL) ? mallat_slice<L>(t, g, p) : g * G + t;
-      store_vec<VEC>(out + slice * plane + e, w[t]);
+      store_vec<VEC>(out + slice * plane + e, w2[t]);
     }
   }
 }
@@ -207,8 +226,10 @@ static int launch_reg(const float* in, float* out, int64_t plane, int64_t p, cud
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // group-fastest chunk order for the Mallat-position gathers at L >= 4
+  constexpr bool GF = !IL && !reads_spatial(OP) && L >= 4;
   WP_PROFILE(kLiftNames[OP], st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP, IL>, in, out, plane, p, nvec, total));
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP, IL, GF>, in, out, plane, p, nvec, total));
   return launch_status();
 }
 
