@@ -22,7 +22,8 @@ Modules:
   wsvd       truncated w-svd (Algorithm 2, Thm 2.5) and sp-w-svd (Sec. IV-B)
   wpinv      Moore-Penrose inverse under the w-product (Def. 2.6, Thm 2.6)
   grad       gradient of <G, A *w B> with respect to A and B (adjoint route)
-  deblur     gradient-descent deblurring objective ||K *w X - Y||^2 + lam||X||^2
+  deblur     two-sided pseudo-inverse deblurring A_V^+ *w B *w (A_H^T)^+ and the
+             gradient-descent objective ||K *w X - Y||^2 + lam||X||^2
   metrics    relative Frobenius error, PSNR (Sec. IV-A)
   quant      emulation of the FP8 (E4M3, one scale per slice) face-product
 
@@ -38,7 +39,7 @@ from .wproduct import facewise, wprod, transpose, identity, trace
 from .wsvd import wsvd, spwsvd
 from .wpinv import wpinv
 from .grad import wprod_grad
-from .deblur import deblur_loss, deblur_grad, deblur_steps
+from .deblur import deblur_loss, deblur_grad, deblur_steps, deblur_pinv
 from .metrics import rel_fro, psnr
 from .quant import e4m3_round, facewise_fp8, wprod_fp8
 
@@ -46,5 +47,5 @@ __all__ = [
     "lift", "ilift", "lift_adjoint", "ilift_adjoint", "split_mallat", "check_levels",
     "dense_lifting_matrix", "facewise", "wprod", "transpose", "identity", "trace",
     "wsvd", "spwsvd", "wpinv", "wprod_grad", "deblur_loss", "deblur_grad",
-    "deblur_steps", "rel_fro", "psnr", "e4m3_round", "facewise_fp8", "wprod_fp8",
+    "deblur_steps", "deblur_pinv", "rel_fro", "psnr", "e4m3_round", "facewise_fp8", "wprod_fp8",
 ]

@@ -1,4 +1,13 @@
-"""Gradient-descent deblurring under the w-product (test oracle).
+"""Deblurring under the w-product (test oracle): the two-sided pseudo-inverse
+reconstruction of Sec. IV-C and a gradient-descent variant.
+
+Two-sided model (Sec. IV-C): a cube X is blurred vertically and horizontally
+by band-constant operators, B = A_V *w X *w A_H^T, and recovered as the
+least-squares solution X = A_V^dagger *w B *w (A_H^T)^dagger
+(`deblur_pinv`, written literally: the pseudo-inverse of the transposed
+operator, Def. 2.2 and Def. 2.6).
+
+Gradient-descent variant.
 
 The paper's deblurring model (Sec. IV-C) observes a blurred cube through a
 w-product with a band-constant blur tensor.  The one-sided form used here,
@@ -15,8 +24,9 @@ gradient here is computed by the adjoint route itself.
 
 import numpy as np
 
-from .wproduct import wprod
+from .wproduct import wprod, transpose
 from .grad import wprod_grad
+from .wpinv import wpinv
 
 
 def deblur_loss(K, X, Y, L, lam):
@@ -40,3 +50,11 @@ def deblur_steps(K, X0, Y, L, lam, eta, steps):
         X = X - eta * deblur_grad(K, X, Y, L, lam)
     losses.append(deblur_loss(K, X, Y, L, lam))
     return X, losses
+
+
+def deblur_pinv(AV, AH, B, L, rtol=None):
+    """X = A_V^dagger *w B *w (A_H^T)^dagger for A_V (p, n1, n1), A_H (p, n2, n2)
+    and B (p, n1, n2); `rtol` is the pseudo-inverse cut-off of `wpinv`."""
+    PV = wpinv(AV, L, rtol)
+    PHt = wpinv(transpose(AH), L, rtol)
+    return wprod(wprod(PV, B, L), PHt, L)

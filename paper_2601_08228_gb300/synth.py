@@ -105,6 +105,16 @@ def blur_operator(n, p, sigma=2.0, taps=9, dtype=np.float64):
     return np.ascontiguousarray(np.broadcast_to(T, (p, n, n))).astype(dtype)
 
 
+def linear_blur_operator(n, p, b=10, dtype=np.float64):
+    """Band-constant linear blur tensor (p, n, n) of the two-sided deblurring
+    experiment (Sec. IV-C): Toeplitz with entries c(|i - j|), c(k) = (b - k) / (3 b)
+    for 0 <= k < b and 0 beyond, as printed (rows sum to about 10/3 at b = 10)."""
+    c = np.array([(b - k) / (3.0 * b) if k < b else 0.0 for k in range(n)])
+    i = np.arange(n)
+    T = c[np.abs(i[:, None] - i[None, :])]
+    return np.ascontiguousarray(np.broadcast_to(T, (p, n, n))).astype(dtype)
+
+
 def unit_noise(shape, seed, dtype=np.float64):
     """iid N(0, 1) array of the given shape."""
     return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
