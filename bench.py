@@ -571,6 +571,28 @@ def _extras(capi, args):
     err_pinv = O.rel_fro(X.cpu().numpy(), O.wpinv(A_h, 3))
     out["wpinv_256x192x192_L3"] = {"ms": t_pinv, "refine_iters": 1, "rel_err": err_pinv}
     del Ad, X, wsp
+    # two-sided pseudo-inverse deblurring (Sec. IV-C) at the Salinas shape: a
+    # synthetic clean cube blurred by the paper's linear blur (b = 10).  The
+    # PaviaU (610 rows) and Botswana (1476 rows) operators have slices larger
+    # than the Jacobi kernels hold (about 568 x 568).
+    for key, (n1, n2, p, L) in (("deblur_pinv_512x217x204_L2", (512, 217, 204, 2)),):
+        Xc = synth.hsi_cube(n1, n2, p, rank=20, noise=0.0, seed=6)
+        AV, AH = synth.linear_blur_operator(n1, p), synth.linear_blur_operator(n2, p)
+        Bb = O.wprod(O.wprod(AV, Xc, L), O.transpose(AH), L)
+        AVd, AHd, Bd = (torch.from_numpy(x.astype(np.float32)).cuda() for x in (AV, AH, Bb))
+        wsd = torch.empty(capi.wp_deblur_pinv_workspace(n1, n2, p, L), dtype=torch.uint8, device="cuda")
+        Xd = capi.wp_deblur_pinv(AVd, AHd, Bd, L, ws=wsd)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(3):
+            Xd = capi.wp_deblur_pinv(AVd, AHd, Bd, L, ws=wsd)
+        b.record()
+        torch.cuda.synchronize()
+        Xg = Xd.cpu().numpy()
+        ref = O.deblur_pinv(AV, AH, Bb, L, rtol=max(n1, n2) * 1.1920929e-7)
+        out[key] = {"ms": a.elapsed_time(b) / 3, "refine_iters": 2, "rel_err": O.rel_fro(Xg, ref),
+                    "psnr_vs_clean": O.psnr(Xg, Xc), "oracle_psnr_vs_clean": O.psnr(ref, Xc)}
+        del AVd, AHd, Bd, Xd, wsd
     # precision study: A 1024x1024x256 by B 1024x512x256, per-slice 10^U[-3,3] scales, L = 4
     A, B = synth.scaled_pair(1024, 1024, 512, 256, seed=0)
     ref = O.wprod(A, B, 4)

@@ -241,6 +241,22 @@ WP_API int wp_deblur_step(const float* K, const float* Y, float* X, int64_t n1, 
                           int L, float lam, float eta, int prec, double* loss, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* ---- two-sided pseudo-inverse deblurring (Sec. IV-C) -------------------- */
+
+/* X = A_V^dagger *w B *w (A_H^T)^dagger, the least-squares reconstruction of
+ * a cube blurred as B = A_V *w X *w A_H^T.  A_V (p, n1, n1), A_H (p, n2, n2),
+ * B and X (p, n1, n2), all device float32, slice-major.  The two
+ * pseudo-inverses are wp_wpinv (cut-off `rtol`, `refine_iters` refinement
+ * steps); (A_H^T)^dagger is applied as (A_H^dagger)^T, and the two
+ * w-products run in precision `prec`.  X must not overlap the inputs.
+ * Limits are those of wp_wpinv for n1 x n1 and n2 x n2 slices (the Jacobi
+ * kernels hold a slice on one CTA cluster: up to about 568 x 568;
+ * WP_ERR_UNSUPPORTED beyond). */
+WP_API int wp_deblur_pinv_workspace(int64_t n1, int64_t n2, int64_t p, int L, int prec, size_t* bytes);
+WP_API int wp_deblur_pinv(const float* AV, const float* AH, const float* B, float* X, int64_t n1, int64_t n2,
+                          int64_t p, int L, double rtol, int refine_iters, int prec, void* ws, size_t ws_bytes,
+                          void* stream);
+
 /* ---- a3: truncated w-svd and sp-w-svd (Algorithm 2, Thm 2.5, Sec. IV-B) -- */
 
 /* C_r = rank-r w-svd of A (p, n1, n2): per wavelet-domain slice a one-sided

@@ -7,7 +7,7 @@ backward.  `synth` holds the seeded synthetic input generators.
 """
 
 from .capi import (  # noqa: F401
-    PREC, WPError, lib, wp_deblur_step, wp_deblur_workspace, wp_facewise, wp_get_device_error,
+    PREC, WPError, lib, wp_deblur_pinv, wp_deblur_step, wp_deblur_workspace, wp_facewise, wp_get_device_error,
     wp_lift_adjoint, wp_lift_forward, wp_lift_inverse, wp_wpinv, wp_wprod, wp_wprod_backward,
     wp_wprod_host, wp_wprod_host_workspace, wp_wprod_noalloc, wp_wprod_workspace, wp_wsvd,
 )

@@ -58,6 +58,8 @@ _SIGNATURES = {
     "wp_launch_count": ([], ctypes.c_uint64),
     "wp_get_device_error": ([_P], _I),
     "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
+    "wp_deblur_pinv_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_deblur_pinv": ([_P, _P, _P, _P, _I64, _I64, _I64, _I, ctypes.c_double, _I, _I, _P, _SZ, _P], _I),
     "wp_profile_begin": ([], _I),
     "wp_profile_only": ([ctypes.c_char_p], _I),
     "wp_profile_end": ([], _I),
@@ -276,6 +278,26 @@ def wp_deblur_workspace(n1, n2, p, L, prec="fp32"):
     nbytes = ctypes.c_size_t(0)
     _check(lib().wp_deblur_workspace(n1, n2, p, L, _prec(prec), ctypes.byref(nbytes)), "wp_deblur_workspace")
     return nbytes.value
+
+
+def wp_deblur_pinv_workspace(n1, n2, p, L, prec="fp32"):
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().wp_deblur_pinv_workspace(n1, n2, p, L, _prec(prec), ctypes.byref(nbytes)),
+           "wp_deblur_pinv_workspace")
+    return nbytes.value
+
+
+def wp_deblur_pinv(AV, AH, B, L, rtol=-1.0, refine_iters=2, prec="fp32", out=None, ws=None):
+    """X = A_V^+ *w B *w (A_H^T)^+ (two-sided deblurring, Sec. IV-C) on the GPU."""
+    _req(AV, "AV"), _req(AH, "AH"), _req(B, "B")
+    p, n1, n2 = B.shape
+    need = wp_deblur_pinv_workspace(n1, n2, p, L, prec)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, B.device)
+    X = torch.empty_like(B) if out is None else _req(out, "out")
+    _check(lib().wp_deblur_pinv(_ptr(AV), _ptr(AH), _ptr(B), _ptr(X), n1, n2, p, L, float(rtol), int(refine_iters),
+                                _prec(prec), _ptr(ws), ws.numel(), _stream()), "wp_deblur_pinv")
+    return X
 
 
 def wp_deblur_step(K, Y, X, L, lam, eta, prec="fp32", loss=None, ws=None):

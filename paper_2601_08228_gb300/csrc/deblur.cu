@@ -125,3 +125,64 @@ extern "C" int wp_deblur_step(const float* K, const float* Y, float* X, int64_t 
   gd_update_kernel<<<grid_elems(n), 256, 0, st>>>(X, C, n, lam, eta);
   return launch_status();
 }
+
+// ---- two-sided pseudo-inverse deblurring (Sec. IV-C) ----------------------------------
+//
+// X = A_V^dagger *w B *w (A_H^T)^dagger: two w-pseudo-inverses (wp_wpinv) and
+// two w-products.  (A_H^T)^dagger = (A_H^dagger)^T (facewise, and the
+// transform commutes with the slice transpose, Thm 2.1), so the second
+// product takes P_H = A_H^dagger with transB.
+
+static int deblur_pinv_layout(int64_t n1, int64_t n2, int64_t p, int L, int prec, Sizer& s, size_t* inner) {
+  size_t a = 0, b = 0, c = 0, d = 0;
+  WP_TRY(wp_wpinv_workspace(n1, n1, p, L, &a));
+  WP_TRY(wp_wpinv_workspace(n2, n2, p, L, &b));
+  WP_TRY(wp_wprod_workspace(n1, n1, n2, p, L, prec, &c));   // P_V *w B
+  WP_TRY(wp_wprod_workspace(n1, n2, n2, p, L, prec, &d));   // T *w P_H^T
+  *inner = std::max(std::max(a, b), std::max(c, d));
+  s.take<float>(size_t(p) * n1 * n1);   // P_V
+  s.take<float>(size_t(p) * n2 * n2);   // P_H
+  s.take<float>(size_t(p) * n1 * n2);   // T = P_V *w B
+  s.take<char>(*inner);
+  return WP_OK;
+}
+
+extern "C" int wp_deblur_pinv_workspace(int64_t n1, int64_t n2, int64_t p, int L, int prec, size_t* bytes) {
+  if (!bytes) return WP_ERR_NULL;
+  if (n1 < 1 || n2 < 1 || p < 1) return WP_ERR_SHAPE;
+  WP_TRY(check_levels(p, L));
+  if (prec < WP_PREC_FP32 || prec > WP_PREC_FP8) return WP_ERR_PREC;
+  Sizer s;
+  size_t inner = 0;
+  WP_TRY(deblur_pinv_layout(n1, n2, p, L, prec, s, &inner));
+  *bytes = s.bytes();
+  return WP_OK;
+}
+
+extern "C" int wp_deblur_pinv(const float* AV, const float* AH, const float* B, float* X, int64_t n1, int64_t n2,
+                              int64_t p, int L, double rtol, int refine_iters, int prec, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (n1 < 1 || n2 < 1 || p < 1) return WP_ERR_SHAPE;
+  WP_TRY(check_levels(p, L));
+  if (!AV || !AH || !B || !X) return WP_ERR_NULL;
+  if (prec < WP_PREC_FP32 || prec > WP_PREC_FP8) return WP_ERR_PREC;
+  if (!aligned16(AV) || !aligned16(AH) || !aligned16(B) || !aligned16(X)) return WP_ERR_ALIGN;
+  const size_t bx = size_t(p) * n1 * n2 * 4;
+  if (overlaps(X, bx, AV, size_t(p) * n1 * n1 * 4) || overlaps(X, bx, AH, size_t(p) * n2 * n2 * 4) ||
+      overlaps(X, bx, B, bx))
+    return WP_ERR_ALIAS;
+  Sizer need;
+  size_t inner_bytes = 0;
+  WP_TRY(deblur_pinv_layout(n1, n2, p, L, prec, need, &inner_bytes));
+  if (!ws || ws_bytes < need.bytes()) return WP_ERR_WORKSPACE;
+  Carver cv(ws, ws_bytes);
+  float* PV = cv.take<float>(size_t(p) * n1 * n1);
+  float* PH = cv.take<float>(size_t(p) * n2 * n2);
+  float* T = cv.take<float>(size_t(p) * n1 * n2);
+  void* inner = cv.take<char>(inner_bytes);
+  if (!cv.ok) return WP_ERR_WORKSPACE;
+  WP_TRY(wp_wpinv(AV, PV, n1, n1, p, L, rtol, refine_iters, inner, inner_bytes, stream));
+  WP_TRY(wp_wpinv(AH, PH, n2, n2, p, L, rtol, refine_iters, inner, inner_bytes, stream));
+  WP_TRY(wp_wprod(PV, B, T, n1, n1, n2, p, L, 0, 0, prec, inner, inner_bytes, stream));
+  return wp_wprod(T, PH, X, n1, n2, n2, p, L, 0, 1, prec, inner, inner_bytes, stream);
+}

@@ -52,6 +52,13 @@ def test_host_validation_needs_no_gpu(libwprod):
     assert L.wp_wprod_workspace(4, 4, 4, 8, 3, 0, ctypes.byref(n)) == 0 and n.value > 0
     assert L.wp_wprod(fake, ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), 4, 4, 4, 8, 3, 0, 0, 0,
                       ctypes.c_void_p(4 << 20), 16, None) == 7           # workspace too small
+    # two-sided pseudo-inverse deblurring
+    assert L.wp_deblur_pinv_workspace(4, 4, 12, 3, 0, ctypes.byref(n)) == 3      # p % 2^L
+    assert L.wp_deblur_pinv_workspace(4, 4, 8, 3, 0, ctypes.byref(n)) == 0 and n.value > 0
+    f2, f3, f4 = ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), ctypes.c_void_p(4 << 20)
+    assert L.wp_deblur_pinv(None, f2, f3, f4, 4, 4, 8, 3, -1.0, 2, 0, fake, 1 << 30, None) == 1   # NULL
+    assert L.wp_deblur_pinv(fake, f2, f3, f3, 4, 4, 8, 3, -1.0, 2, 0, fake, 1 << 30, None) == 11  # X aliases B
+    assert L.wp_deblur_pinv(fake, f2, f3, f4, 4, 4, 8, 3, -1.0, 2, 0, fake, 16, None) == 7        # workspace
     # host-buffer w-product: chunks of whole tube groups, validated before any copy
     assert L.wp_wprod_host_workspace(4, 4, 4, 16, 3, 0, 12, ctypes.byref(n)) == 2   # 12 % 2^3 != 0
     assert L.wp_wprod_host_workspace(4, 4, 4, 12, 3, 0, 0, ctypes.byref(n)) == 3    # p % 2^L
