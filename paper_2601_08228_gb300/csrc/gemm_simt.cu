@@ -4,8 +4,7 @@
 // Row-major storage.  op(A[b]) is M x K: A[b] is M x K, or K x M if transA.
 // op(B[b]) is K x N: B[b] is K x N, or N x K if transB.  C[b] is M x N.
 //
-// 128 x 128 x 8 CTA tile, 256 threads, 8 x 8 outputs per thread (two 4 x 4
-// quadrants so that shared-memory reads are conflict-free float4 broadcasts),
+// 128 x 128 x 16 CTA tile, 256 threads, 8 x 8 outputs per thread,
 // register-staged double buffering of the shared-memory tiles.  Ragged edges
 // are zero-filled on load and masked on store.
 
@@ -13,65 +12,76 @@
 
 namespace wp {
 
-constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8;
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16;
 
+// Eight consecutive elements base[row * ld + c0 .. c0 + 7] (zero outside
+// row_ext x c_ext); 16-byte loads when `vec` (c_ext % 4 == 0, 16-byte base).
+__device__ __forceinline__ void sg_load8(const float* __restrict__ base, int64_t ld, int row, int row_ext, int c0,
+                                         int c_ext, bool vec, float (&r)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r[i] = 0.f;
+  if (row >= row_ext) return;
+  const float* src = base + int64_t(row) * ld + c0;
+  if (vec) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (c0 + 4 * h < c_ext) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(src + 4 * h));
+        r[4 * h] = v.x; r[4 * h + 1] = v.y; r[4 * h + 2] = v.z; r[4 * h + 3] = v.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (c0 + i < c_ext) r[i] = __ldg(src + i);
+  }
+}
+
+// 128 x 128 x 16 CTA tile, 256 threads, 8 x 8 outputs per thread (two 4 x 4
+// quadrants: conflict-free float4 shared reads), tiles staged k-major in
+// shared memory, the next k-tile's global loads (8 consecutive elements of
+// A and of B per thread, 16-byte vectors where the storage allows) in
+// registers while the current one is multiplied.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) sgemm_batched_kernel(
+__global__ void __launch_bounds__(256, 2) sgemm_batched_kernel(
     const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C, int M, int N,
-    int K, int64_t sA, int64_t sB, int64_t sC, int batch) {
+    int K, int64_t sA, int64_t sB, int64_t sC, int batch, int va, int vb) {
   __shared__ __align__(16) float As[2][SG_BK][SG_BM];
   __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * SG_BM, n0 = blockIdx.x * SG_BN;
+  // load roles: along the contiguous dimension, 8 elements per thread; for
+  // k-contiguous operands the 32 lanes of a warp take 32 rows (conflict-free
+  // transposing shared stores)
+  const int a_row = TA ? (tid >> 4) : (tid & 127), a_c = TA ? (tid & 15) * 8 : (tid >> 7) * 8;
+  const int b_row = TB ? (tid & 127) : (tid >> 4), b_c = TB ? (tid >> 7) * 8 : (tid & 15) * 8;
 
   for (int b = blockIdx.z; b < batch; b += gridDim.z) {
     const float* Ab = A + int64_t(b) * sA;
     const float* Bb = B + int64_t(b) * sB;
     float* Cb = C + int64_t(b) * sC;
-
-    // per-thread load coordinates (4 elements of A and 4 of B per k-tile)
-    float ra[4], rb[4];
-    auto load_a = [&](int k0) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        int m, k;
-        if (!TA) { m = tid / 2; k = (tid % 2) * 4 + i; }     // k contiguous in memory
-        else { k = tid / 32; m = (tid % 32) * 4 + i; }       // m contiguous in memory
-        const int gm = m0 + m, gk = k0 + k;
-        float v = 0.f;
-        if (gm < M && gk < K) v = TA ? Ab[int64_t(gk) * M + gm] : Ab[int64_t(gm) * K + gk];
-        ra[i] = v;
-      }
+    float ra[8], rb[8];
+    auto load = [&](int k0) {
+      if (TA) sg_load8(Ab, M, k0 + a_row, K, m0 + a_c, M, va, ra);     // stored K x M
+      else sg_load8(Ab, K, m0 + a_row, M, k0 + a_c, K, va, ra);        // stored M x K
+      if (TB) sg_load8(Bb, K, n0 + b_row, N, k0 + b_c, K, vb, rb);     // stored N x K
+      else sg_load8(Bb, N, k0 + b_row, K, n0 + b_c, N, vb, rb);        // stored K x N
     };
-    auto store_a = [&](int buf) {
+    auto store = [&](int buf) {
+      if (TA) {
+        *reinterpret_cast<float4*>(&As[buf][a_row][a_c]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+        *reinterpret_cast<float4*>(&As[buf][a_row][a_c + 4]) = make_float4(ra[4], ra[5], ra[6], ra[7]);
+      } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        int m, k;
-        if (!TA) { m = tid / 2; k = (tid % 2) * 4 + i; }
-        else { k = tid / 32; m = (tid % 32) * 4 + i; }
-        As[buf][k][m] = ra[i];
+        for (int i = 0; i < 8; ++i) As[buf][a_c + i][a_row] = ra[i];
       }
-    };
-    auto load_b = [&](int k0) {
+      if (TB) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        int n, k;
-        if (!TB) { k = tid / 32; n = (tid % 32) * 4 + i; }   // n contiguous in memory
-        else { n = tid / 2; k = (tid % 2) * 4 + i; }         // k contiguous in memory
-        const int gn = n0 + n, gk = k0 + k;
-        float v = 0.f;
-        if (gn < N && gk < K) v = TB ? Bb[int64_t(gn) * K + gk] : Bb[int64_t(gk) * N + gn];
-        rb[i] = v;
-      }
-    };
-    auto store_b = [&](int buf) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        int n, k;
-        if (!TB) { k = tid / 32; n = (tid % 32) * 4 + i; }
-        else { n = tid / 2; k = (tid % 2) * 4 + i; }
-        Bs[buf][k][n] = rb[i];
+        for (int i = 0; i < 8; ++i) Bs[buf][b_c + i][b_row] = rb[i];
+      } else {
+        *reinterpret_cast<float4*>(&Bs[buf][b_row][b_c]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+        *reinterpret_cast<float4*>(&Bs[buf][b_row][b_c + 4]) = make_float4(rb[4], rb[5], rb[6], rb[7]);
       }
     };
 
@@ -82,17 +92,12 @@ __global__ void __launch_bounds__(256) sgemm_batched_kernel(
       for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
     const int ktiles = (K + SG_BK - 1) / SG_BK;
-    load_a(0);
-    load_b(0);
-    store_a(0);
-    store_b(0);
+    load(0);
+    store(0);
     __syncthreads();
     for (int kt = 0; kt < ktiles; ++kt) {
       const int cur = kt & 1;
-      if (kt + 1 < ktiles) {
-        load_a((kt + 1) * SG_BK);
-        load_b((kt + 1) * SG_BK);
-      }
+      if (kt + 1 < ktiles) load((kt + 1) * SG_BK);
 #pragma unroll
       for (int k = 0; k < SG_BK; ++k) {
         const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
@@ -106,10 +111,7 @@ __global__ void __launch_bounds__(256) sgemm_batched_kernel(
 #pragma unroll
           for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
-      if (kt + 1 < ktiles) {
-        store_a(cur ^ 1);
-        store_b(cur ^ 1);
-      }
+      if (kt + 1 < ktiles) store(cur ^ 1);
       __syncthreads();
     }
 
@@ -146,11 +148,18 @@ int sgemm_batched(const float* A, const float* B, float* C, int M, int N, int K,
   const int64_t sA = int64_t(M) * K, sB = int64_t(K) * N, sC = int64_t(M) * N;
   dim3 grid((N + SG_BN - 1) / SG_BN, (M + SG_BM - 1) / SG_BM, std::min(batch, 65535));
   if (grid.y > 65535) return WP_ERR_SHAPE;
+  // 16-byte loads where each operand's contiguous dimension is a multiple of 4
+  const int va = aligned16(A) && ((transA ? M : K) % 4 == 0);
+  const int vb = aligned16(B) && ((transB ? K : N) % 4 == 0);
   WP_PROFILE("sgemm_fp32", st);
-  if (!transA && !transB) sgemm_batched_kernel<false, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch);
-  else if (!transA && transB) sgemm_batched_kernel<false, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch);
-  else if (transA && !transB) sgemm_batched_kernel<true, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch);
-  else sgemm_batched_kernel<true, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch);
+  if (!transA && !transB)
+    sgemm_batched_kernel<false, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch, va, vb);
+  else if (!transA && transB)
+    sgemm_batched_kernel<false, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch, va, vb);
+  else if (transA && !transB)
+    sgemm_batched_kernel<true, false><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch, va, vb);
+  else
+    sgemm_batched_kernel<true, true><<<grid, 256, 0, st>>>(A, B, C, M, N, K, sA, sB, sC, batch, va, vb);
   return launch_status();
 }
 
