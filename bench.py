@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
-    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "wprod", "wprod_fp8", "jacobi", "batched"],
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "sgemm", "wprod", "wprod_fp8", "jacobi", "batched"],
                     default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
@@ -637,6 +637,11 @@ def run_profile_case(case):
         B = torch.rand((64, 1024, 512), device="cuda")
         for prec in ("bf16", "bf16x3"):
             capi.wp_facewise(A, B, prec=prec)
+    elif case == "sgemm":
+        # FP32 SIMT face-product of the benchmark's shape: 192 slices of 256 x 256 (2 x 50 MB in)
+        A = torch.rand((192, 256, 256), device="cuda")
+        B = torch.rand((192, 256, 256), device="cuda")
+        capi.wp_facewise(A, B, prec="fp32")
     elif case == "wprod":
         A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
         capi.wp_wprod(A, B, WORKLOAD["L"], prec="bf16x3")
