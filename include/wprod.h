@@ -324,9 +324,11 @@ typedef struct {
  * with tune = 1, times candidate CTA sizes for the face-product and Jacobi
  * phases on the planned work (this runs those phases; outputs are not
  * final until wp_batched_run).  wp_batched_run launches the four phases
- * (lifting, face-products, Jacobi SVD with rank-r rebuild, inverse lifting);
- * it neither allocates, copies nor synchronises, so it can be captured in a
- * CUDA graph and replayed while the workspace and the items' buffers live. */
+ * (lifting, face-products, Jacobi SVD with rank-r rebuild, inverse lifting;
+ * the Jacobi phase as up to three launches, one per slice-width class of the
+ * plan); it neither allocates, copies nor synchronises, so it can be
+ * captured in a CUDA graph and replayed while the workspace and the items'
+ * buffers live. */
 WP_API int wp_batched_workspace(const wp_batch_item* items, int count, size_t* bytes);
 WP_API int wp_batched_plan(const wp_batch_item* items, int count, int tune, void* ws, size_t ws_bytes,
                            wp_batch_plan* plan, void* stream);
