@@ -1,0 +1,180 @@
+"""CPU simulations of the index arithmetic of the streaming kernels (the
+mappings from grid / block / thread indices to tensor elements, restated
+from the kernels' formulas), checked for exact coverage and in-bounds
+accesses over ragged shapes.  Compute-sanitizer is not available to these
+builds; these checks stand in for its bounds checking."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+
+def cdiv(a, b):
+    return (a + b - 1) // b
+
+
+# ---- lift_reg_kernel: grid-stride and group-fastest chunk orders -------------------
+
+def lift_items(p, L, plane, vec, grid, gf, threads=256):
+    """(g, e) visited by every (CTA, thread) of lift_reg_kernel."""
+    G = 1 << L
+    m = p >> L
+    nvec = plane // vec
+    total = m * nvec
+    nchunk = cdiv(nvec, threads)
+    seen = []
+    for bx in range(grid):
+        for t in range(threads):
+            if gf:
+                w, stride, nwork = bx, grid, m * nchunk
+            else:
+                w, stride, nwork = bx * threads + t, grid * threads, total
+            while w < nwork:
+                if gf:
+                    g, iv = w % m, (w // m) * threads + t
+                    if iv < nvec:
+                        seen.append((g, iv * vec))
+                else:
+                    g, iv = w // nvec, w % nvec
+                    seen.append((g, iv * vec))
+                w += stride
+    return seen
+
+
+@pytest.mark.parametrize("p,L,plane,vec,grid", [(16, 4, 4096, 4, 7), (32, 5, 2 * 257, 2, 5), (24, 3, 85, 1, 3),
+                                                (64, 4, 1000, 4, 9)])
+@pytest.mark.parametrize("gf", [False, True])
+def test_lift_chunk_orders_cover_every_item_once(p, L, plane, vec, grid, gf):
+    seen = lift_items(p, L, plane, vec, grid, gf)
+    want = {(g, e) for g in range(p >> L) for e in range(0, plane - vec + 1, vec)}
+    assert len(seen) == len(set(seen)) == len(want) and set(seen) == want
+    G = 1 << L
+    assert all((g * G + G - 1) * plane + e + vec - 1 < p * plane for g, e in seen)
+
+
+# ---- transpose_bytes_kernel: (batch, R, C) -> (batch, C, Rp) in 64 x 64 tiles -------
+
+def transpose_bytes_accesses(R, C, Rp, batch, vec16):
+    T = 64
+    reads, writes = [], []
+    for bz, by, bx in itertools.product(range(batch), range(cdiv(Rp, T)), range(cdiv(C, T))):
+        c0, r0 = bx * T, by * T
+        for tid in range(256):
+            i, j = tid >> 2, (tid & 3) * 16
+            r, c = r0 + i, c0 + j
+            if r < R:
+                if vec16 and c + 15 < C:
+                    reads += [(bz, r, c + k) for k in range(16)]
+                else:
+                    reads += [(bz, r, c + k) for k in range(16) if c + k < C]
+            cc, k = tid & 63, tid >> 6
+            c, rs = c0 + cc, r0 + k * 16
+            if c < C and rs < Rp:
+                writes += [(bz, c, rs + q) for q in range(16)]
+    return reads, writes
+
+
+@pytest.mark.parametrize("R,C,batch", [(17, 40, 2), (64, 64, 1), (100, 33, 2), (16, 128, 1)])
+def test_transpose_bytes_covers_the_output_once(R, C, batch):
+    Rp = cdiv(R, 16) * 16
+    for vec16 in ([False, True] if C % 16 == 0 else [False]):
+        reads, writes = transpose_bytes_accesses(R, C, Rp, batch, vec16)
+        assert all(r < R and c < C for _, r, c in reads)
+        want = {(b, c, r) for b in range(batch) for c in range(C) for r in range(Rp)}
+        assert len(writes) == len(set(writes)) and set(writes) == want
+
+
+# ---- split_transpose4_kernel: (p, R, C) fp32 -> (p, C, Rp) bf16, 64 x 64 tiles -------
+
+@pytest.mark.parametrize("R,C,Rp,batch", [(17, 40, 24, 2), (64, 64, 64, 1), (100, 36, 104, 1), (8, 132, 8, 1)])
+def test_split_transpose4_covers_the_output_once(R, C, Rp, batch):
+    assert C % 4 == 0 and Rp % 8 == 0 and Rp >= R
+    T = 64
+    writes, reads = [], []
+    for b, by, bx in itertools.product(range(batch), range(cdiv(Rp, T)), range(cdiv(C, T))):
+        c0, r0 = bx * T, by * T
+        for tid in range(256):
+            for k in range(4):
+                i, j = (tid >> 4) + 16 * k, (tid & 15) * 4
+                r, c = r0 + i, c0 + j
+                if r < R and c < C:
+                    assert c + 3 < C          # whole 16-byte vector inside the row
+                    reads += [(b, r, c + q) for q in range(4)]
+            for k in range(2):
+                w = tid + 256 * k
+                cc, chunk = w & 63, w >> 6
+                c, rs = c0 + cc, r0 + chunk * 8
+                if c < C and rs < Rp:
+                    writes += [(b, c, rs + q) for q in range(8)]
+    want = {(b, c, r) for b in range(batch) for c in range(C) for r in range(Rp)}
+    assert len(writes) == len(set(writes)) and set(writes) == want
+    assert {(b, r, c) for b, r, c in reads} == {(b, r, c) for b in range(batch) for r in range(R) for c in range(C)}
+
+
+# ---- batched lift: descriptor chunks -----------------------------------------------
+
+def batched_vec(L, plane, a16):
+    vm = 4 if L <= 2 else (2 if L == 3 else 1)
+    if vm >= 4 and plane % 4 == 0 and a16:
+        return 4
+    if vm >= 2 and plane % 2 == 0 and a16:
+        return 2
+    return 1
+
+
+@pytest.mark.parametrize("plane,p,L", [(16 * 17, 32, 2), (40 * 41, 64, 3), (63 * 17, 128, 5), (1, 4, 1),
+                                       (64 * 64, 32, 1)])
+def test_batched_lift_chunks_cover_each_tensor_once(plane, p, L):
+    vec = batched_vec(L, plane, True)
+    cpg = cdiv(plane, 256 * vec)
+    seen = []
+    for local in range((p >> L) * cpg):
+        g = local // cpg
+        for t in range(256):
+            e = ((local % cpg) * 256 + t) * vec
+            if e < plane:
+                assert e + vec <= plane
+                seen += [(g, e + q) for q in range(vec)]
+    want = {(g, e) for g in range(p >> L) for e in range(plane)}
+    assert len(seen) == len(set(seen)) and set(seen) == want
+
+
+# ---- FP8 passes: lift_amax_kernel (2-D grid) and lift_quant_rows_kernel (two operands) --
+
+@pytest.mark.parametrize("p,L,plane_a,plane_b,vec,bx", [(16, 4, 64 * 80, 80 * 48, 2, 3), (8, 2, 33 * 17, 17 * 40, 1, 5),
+                                                       (24, 3, 96 * 64, 64 * 72, 4, 2)])
+def test_fp8_amax_grid_covers_both_operands_once(p, L, plane_a, plane_b, vec, bx):
+    m = p >> L
+    seen = []
+    for by in range(2 * m):
+        op, g = (0, by) if by < m else (1, by - m)
+        nvec = (plane_a if op == 0 else plane_b) // vec
+        for x in range(bx):
+            for t in range(256):
+                i = x * 256 + t
+                while i < nvec:
+                    seen.append((op, g, i))
+                    i += bx * 256
+    want = {(0, g, i) for g in range(m) for i in range(plane_a // vec)} | \
+           {(1, g, i) for g in range(m) for i in range(plane_b // vec)}
+    assert len(seen) == len(set(seen)) and set(seen) == want
+
+
+@pytest.mark.parametrize("p,L,plane_a,plane_b,vec,blocks", [(16, 4, 64 * 80, 80 * 48, 2, 7), (8, 2, 33 * 17, 17 * 40, 1, 3)])
+def test_fp8_quant_rows_two_operands_once(p, L, plane_a, plane_b, vec, blocks):
+    m = p >> L
+    items0 = m * (plane_a // vec)
+    total = items0 + m * (plane_b // vec)
+    seen = []
+    for it in range(total):       # the grid-stride loop visits 0 .. total - 1 once
+        first = it < items0
+        item = it if first else it - items0
+        nvec = (plane_a if first else plane_b) // vec
+        seen.append((0 if first else 1, item // nvec, (item % nvec) * vec))
+    want = {(0, g, e) for g in range(m) for e in range(0, plane_a, vec)} | \
+           {(1, g, e) for g in range(m) for e in range(0, plane_b, vec)}
+    assert len(seen) == len(set(seen)) and set(seen) == want
+    # the grid-stride loop itself: every item index exactly once
+    visits = [it for b in range(blocks) for t in range(256) for it in range(b * 256 + t, total, blocks * 256)]
+    assert sorted(visits) == list(range(total))
