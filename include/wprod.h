@@ -36,6 +36,10 @@
  *   detected inside kernels (an expired bounded wait, a Jacobi sweep limit)
  *   are recorded in a per-device status word that wp_get_device_error()
  *   returns and clears.  Nothing calls abort() and no kernel traps.
+ * Device reset.  The library keeps per-device addresses of its own device
+ *   variables (status word, counters, scratch array) from the first call on
+ *   each device.  cudaDeviceReset() destroys them: calls after a reset in the
+ *   same process are not supported.
  */
 #ifndef WPROD_H
 #define WPROD_H
@@ -113,10 +117,32 @@ WP_API int wp_profile_get(int index, char* name, int name_len, int64_t* launches
  * largest sweep count of any slice. */
 WP_API int wp_jacobi_stats(int64_t* total_sweeps, int* max_sweeps);
 
+/* Sweep limit of the one-sided Jacobi SVD used by wp_wsvd, wp_wpinv,
+ * wp_deblur_pinv and wp_batched_run (Algorithm 2 takes its facewise SVDs
+ * from a library routine; the iteration limit is this library's own).
+ * Default 40; 1 <= max_sweeps <= 1000, else WP_ERR_SHAPE and no change.
+ * Applies to launches enqueued after the call (a CUDA graph keeps the limit
+ * it was captured with).  A slice still rotating after the last allowed
+ * sweep keeps its partial result and sets WP_ERR_NOT_CONVERGED in the device
+ * status word (wp_get_device_error).  Process-wide; not synchronised with
+ * calls in flight on other host threads. */
+WP_API int wp_set_jacobi_max_sweeps(int max_sweeps);
+
 /* Synchronise `stream`, then return and clear the device status word of the
  * current device (WP_OK if no kernel reported a fault since the last call).
  * Returns WP_ERR_CUDA if the synchronisation itself fails. */
 WP_API int wp_get_device_error(void* stream);
+
+/* Test of the failure-detection path of the bounded device-side waits (the
+ * paper has no counterpart).  Launches one kernel that waits, with the given
+ * limit, on a barrier that nothing ever completes: which = 0 uses the
+ * CTA-scope wait of the tensor-core kernels, which = 1 the cluster-scope wait
+ * of the Jacobi kernels.  The wait expires after limit_ns nanoseconds
+ * (1e3 <= limit_ns <= 1e8, else WP_ERR_SHAPE and nothing is launched), sets
+ * WP_ERR_TIMEOUT in the device status word and the kernel returns normally:
+ * nothing is in flight on the barrier, so the context stays usable.  Read
+ * the result with wp_get_device_error(). */
+WP_API int wp_selftest_bounded_wait(int which, int64_t limit_ns, void* stream);
 
 /* ---- a1 / a4: lifting along mode 3 (Sec. II-A, Eq. 1-3, Algorithm 1) ---- */
 
@@ -203,7 +229,11 @@ WP_API int wp_wprod_host(const float* A, const float* B, float* C, int64_t n1, i
  *   - Requests whose wp_wprod_workspace() size exceeds the array return
  *     WP_ERR_WORKSPACE and launch nothing.
  *   - The first call on each device looks up the array's device address on
- *     that device (the device current at the time of the call).
+ *     that device (the device current at the time of the call) and keeps it
+ *     for the rest of the process.  Make that first call before any stream
+ *     capture.  cudaDeviceReset() invalidates the kept address (as it does
+ *     every device address the library keeps, see "Device reset" above):
+ *     do not call this entry point after a device reset.
  *   - All calls share the one array.  Calls whose kernels overlap on the GPU
  *     (different streams, or different host threads on one device) race on
  *     it and give wrong results: serialise them, e.g. on one stream.

@@ -25,6 +25,10 @@ STATUS_NAMES = {
 }
 
 
+# Named status codes (include/wprod.h wp_status).
+globals().update({name: code for code, name in STATUS_NAMES.items()})
+
+
 class WPError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -58,6 +62,8 @@ _SIGNATURES = {
     "wp_launch_count": ([], ctypes.c_uint64),
     "wp_get_device_error": ([_P], _I),
     "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
+    "wp_set_jacobi_max_sweeps": ([_I], _I),
+    "wp_selftest_bounded_wait": ([_I, _I64, _P], _I),
     "wp_deblur_pinv_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_deblur_pinv": ([_P, _P, _P, _P, _I64, _I64, _I64, _I, ctypes.c_double, _I, _I, _P, _SZ, _P], _I),
     "wp_profile_begin": ([], _I),
@@ -417,6 +423,16 @@ def wp_jacobi_stats():
     t, m = _I64(0), _I(0)
     _check(lib().wp_jacobi_stats(ctypes.byref(t), ctypes.byref(m)), "wp_jacobi_stats")
     return int(t.value), int(m.value)
+
+
+def wp_set_jacobi_max_sweeps(n):
+    """Set the Jacobi sweep limit of later launches (default 40)."""
+    _check(lib().wp_set_jacobi_max_sweeps(int(n)), "wp_set_jacobi_max_sweeps")
+
+
+def wp_selftest_bounded_wait(which, limit_ns):
+    """Launch a wait that must expire after limit_ns (see include/wprod.h)."""
+    _check(lib().wp_selftest_bounded_wait(int(which), int(limit_ns), _stream()), "wp_selftest_bounded_wait")
 
 
 def wp_launch_count():

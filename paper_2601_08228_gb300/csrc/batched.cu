@@ -379,7 +379,7 @@ static int launch_batched_jacobi_t(const BItem* items, const int2* units, int64_
   const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * per_sm);
   WP_PROFILE("batched_jacobi", st);
   batched_jacobi_kernel<PPW, NW><<<unsigned(std::max<int64_t>(grid, 1)), NW * 32, smem, st>>>(
-      items, units, n, 40, device_status_ptr(), jacobi_stats_ptr());
+      items, units, n, jacobi_max_sweeps(), device_status_ptr(), jacobi_stats_ptr());
   return launch_status();
 }
 

@@ -15,15 +15,23 @@
 //           wavelet-domain slices, after the lifting has mixed the 2^L
 //           spatial slices of a group.
 //
-// Pipeline (one CTA per 128 x BN output tile of one slice, 6 warps):
-//   warp 0      TMA producer: loads the K-major BF16 tiles of A (128 x 64)
-//               and B (BN x 64) with 128-byte swizzle into a STAGES-deep ring
-//   warp 1      allocates TMEM; one lane issues tcgen05.mma (M = 128, N = BN,
-//               K = 16) and frees ring slots with tcgen05.commit
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator, masked FP32 stores
+// Kernels
+//   tc_gemm_kernel        persistent: one CTA per SM walks every (slice, row
+//                         tile, column tile) tile of 128 x BN; warp 0 lane 0
+//                         issues TMA loads of the 128-byte-swizzled BF16 / E4M3
+//                         tiles into a STAGES-deep ring, warp 1 owns TMEM and
+//                         one lane issues tcgen05.mma (M = 128, N = BN), warps
+//                         2-5 drain one of two TMEM accumulators (tcgen05.ld)
+//                         and store C through swizzled shared-memory staging and
+//                         TMA bulk stores while the next tile is multiplied.
+//   tc_gemm_ilift_kernel  one CTA per 128 x (512 / 2^L) tile of all 2^L slices
+//                         of a tube group, 2^L TMEM accumulators, inverse lift
+//                         (Eq. 3) across them in the epilogue: the fused
+//                         w-product for small slices.
 // Operands are prepared by `split` kernels that round the FP32 wavelet-domain
 // slices to BF16 hi (/ lo) and, where the stored layout is not K-major,
-// transpose through shared memory.  Every mbarrier wait is bounded.
+// transpose through shared memory, or by lift-and-split kernels that also
+// apply the forward transform.  Every mbarrier wait is bounded.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -801,13 +809,10 @@ struct FusedLayout {
   static constexpr int CH = 64 / G < 16 ? 64 / G : 16;  // columns per epilogue chunk (registers: G * CH = 64)
 };
 
-// MC > 1: the MC CTAs of a cluster (consecutive N tiles of one row tile and
-// tube group) share every A tile: each fetches BM / MC of its rows and
-// multicasts them to all, and a stage is refilled only after all MC CTAs
-// have consumed it (their MMA commits arrive on every CTA's `empty`).
-// BMN: B is MN-major -- W(B) in its natural (K rows, N contiguous) layout,
+// Each CTA loads its own A tiles; the N tiles of one row tile re-read them
+// through L2.  BMN: B is MN-major -- W(B) in its natural (K rows, N contiguous) layout,
 // loaded as 64-column boxes -- instead of K-major.
-template <int L, int NPROD, int STAGES, int TMEM, int MC, bool BMN>
+template <int L, int NPROD, int STAGES, int TMEM, bool BMN>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_ilift_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                          const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
@@ -821,9 +826,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr bool TMA_EPI = (BN >= 32) && (CH >= 4);
   constexpr int SPP = fused_store_slices(G, BN, STAGES * Lay::STAGE);
   static_assert(!BMN || BN % 64 == 0, "MN-major B needs 64-column blocks");
-  static_assert(BM % MC == 0, "A rows split over the cluster");
-  constexpr int AR = BM / MC;                                  // A rows fetched by this CTA
-  constexpr uint16_t MASK = uint16_t((1u << MC) - 1u);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFF);
@@ -845,7 +847,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], MC);
+      ptx::mbar_init(&empty[s], 1);
     }
     ptx::mbar_init(accum, 1);
     ptx::fence_mbar_init();
@@ -854,10 +856,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
-  // every CTA's barriers are initialised before any peer multicasts into it
-  if constexpr (MC > 1) cg::this_cluster().sync();
   const uint32_t tmem = *tmem_slot;
-  const int crank = (MC > 1) ? int(cg::this_cluster().block_rank()) : 0;
   bool ok = true;
 
   if (warp == 0 && lane == 0) {
@@ -874,14 +873,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (it >= STAGES) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
       if (!ok) break;
       ptx::mbar_arrive_expect_tx(&full[s], Lay::STAGE);
-      if constexpr (MC > 1) {
-        ptx::tma_load_3d_mc(a_tile(s, 0) + crank * AR * 128, &tmAh, kb * BK, m0 + crank * AR, z, &full[s], MASK);
-        if (NPROD == 3)
-          ptx::tma_load_3d_mc(a_tile(s, 1) + crank * AR * 128, &tmAl, kb * BK, m0 + crank * AR, z, &full[s], MASK);
-      } else {
-        ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BK, m0, z, &full[s]);
-        if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BK, m0, z, &full[s]);
-      }
+      ptx::tma_load_3d(a_tile(s, 0), &tmAh, kb * BK, m0, z, &full[s]);
+      if (NPROD == 3) ptx::tma_load_3d(a_tile(s, 1), &tmAl, kb * BK, m0, z, &full[s]);
       if constexpr (BMN) {
 #pragma unroll
         for (int j = 0; j < BN / 64; ++j) {
@@ -925,8 +918,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ptx::mma_bf16(d, al, bh, idesc, 1u);
         }
       }
-      if constexpr (MC > 1) ptx::mma_commit_mc(&empty[s], MASK);
-      else ptx::mma_commit(&empty[s]);
+      ptx::mma_commit(&empty[s]);
     }
     ptx::mma_commit(accum);
   } else if (warp >= 2) {
@@ -1032,8 +1024,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
     ptx::tmem_dealloc(tmem, TMEM);
   }
-  // no CTA leaves while a peer's multicast or commit can still reach it
-  if constexpr (MC > 1) cg::this_cluster().sync();
 }
 
 }  // namespace tc
@@ -1302,15 +1292,14 @@ static int launch_lift_split_rows(const float* A, __nv_bfloat16* hi, __nv_bfloat
 
 // One CTA per SM with all 512 TMEM columns (measured faster at L = 3 than
 // two CTAs with 256 columns each: narrower N = 32 tiles, 2-stage rings).
-// MC: CTAs of a cluster sharing A tiles by multicast (consecutive N tiles).
-template <int L, int NPROD, int MC, bool BMN>
+template <int L, int NPROD, bool BMN>
 static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
                         float* C, int64_t M, int64_t N, int64_t K, int64_t p, cudaStream_t st) {
   constexpr int TMEM = 512;
   using Probe = tc::FusedLayout<L, NPROD, 1, TMEM>;
   constexpr int STAGES = std::min(6, 196608 / Probe::STAGE);
   using Lay = tc::FusedLayout<L, NPROD, STAGES, TMEM>;
-  auto kern = tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM, MC, BMN>;
+  auto kern = tc::tc_gemm_ilift_kernel<L, NPROD, STAGES, TMEM, BMN>;
   static bool attr = false;
   if (!attr) {
     WP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
@@ -1321,17 +1310,13 @@ static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUte
   cfg.blockDim = dim3(tc::THREADS, 1, 1);
   cfg.dynamicSmemBytes = Lay::SMEM;
   cfg.stream = st;
-  cudaLaunchAttribute attrs[2];
-  attrs[0].id = cudaLaunchAttributeClusterDimension;
-  attrs[0].val.clusterDim.x = MC;
-  attrs[0].val.clusterDim.y = 1;
-  attrs[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attrs[1];
   // programmatic serialisation: the prologue may overlap the operand
   // preparation kernel; the kernel waits for it before its first load
-  attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attrs[1].val.programmaticStreamSerializationAllowed = 1;
+  attrs[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attrs[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attrs;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = 1;
   // output tensor map for the TMA-store epilogue: (p, M, N) FP32 with N % 4
   // == 0 (16-byte row stride), boxes of 32 columns x 128 rows x SPP slices
   constexpr int SPP = tc::fused_store_slices(Lay::G, Lay::BN, STAGES * Lay::STAGE);
@@ -1345,15 +1330,6 @@ static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUte
   WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, mc, tma_store, C, int(M), int(N), int(K), p,
                                  device_status_ptr()));
   return launch_status();
-}
-
-template <int L, int NPROD, bool BMN>
-static int launch_fused_mc(int mc, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
-                           const CUtensorMap& bl, float* C, int64_t M, int64_t N, int64_t K, int64_t p,
-                           cudaStream_t st) {
-  if (mc == 4) return launch_fused<L, NPROD, 4, BMN>(ah, al, bh, bl, C, M, N, K, p, st);
-  if (mc == 2) return launch_fused<L, NPROD, 2, BMN>(ah, al, bh, bl, C, M, N, K, p, st);
-  return launch_fused<L, NPROD, 1, BMN>(ah, al, bh, bl, C, M, N, K, p, st);
 }
 
 template <int L>
@@ -1381,12 +1357,8 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
   }
   constexpr int BN = tc::FusedLayout<L, 1, 1, 512>::BN;
   constexpr bool BMN = (L <= 3);
-  // A tiles shared by the cluster's N tiles: as many CTAs as divide the N tiles (at most 4)
-  const int64_t ntiles = (n4 + BN - 1) / BN;
-  const int mc = (ntiles % 4 == 0) ? 4 : (ntiles % 2 == 0) ? 2 : 1;
-  const int arows = tc::BM / mc;
-  WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, arows));
-  if (x3) WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, arows));
+  WP_TRY(make_map(&mah, Ah, n2, Kp, n1, p, tc::BM));
+  if (x3) WP_TRY(make_map(&mal, Al, n2, Kp, n1, p, tc::BM));
   if constexpr (BMN) {
     // W(B) in its natural layout (K rows of n4 columns), 64-column boxes
     const int64_t Np = pad8(n4);
@@ -1400,8 +1372,8 @@ static int fused_levels(const float* A, const float* B, float* C, int64_t n1, in
     WP_TRY(make_map(&mbh, Bh, n2, Kp, n4, p, BN));
     if (x3) WP_TRY(make_map(&mbl, Bl, n2, Kp, n4, p, BN));
   }
-  if (x3) return launch_fused_mc<L, 3, BMN>(mc, mah, mal, mbh, mbl, C, n1, n4, n2, p, st);
-  return launch_fused_mc<L, 1, BMN>(mc, mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
+  if (x3) return launch_fused<L, 3, BMN>(mah, mal, mbh, mbl, C, n1, n4, n2, p, st);
+  return launch_fused<L, 1, BMN>(mah, mah, mbh, mbh, C, n1, n4, n2, p, st);
 }
 
 // Elements per thread of the FP8 lift passes: G x VEC values stay in

@@ -43,5 +43,9 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
 bool jacobi_supported(int n1, int n2);
 // Device address of the Jacobi sweep counters ([0] total slice-sweeps, [1] max).
 unsigned long long* jacobi_stats_ptr();
+// Sweep limit passed to every Jacobi launch (default kJacobiMaxSweeps; set by
+// wp_set_jacobi_max_sweeps).
+constexpr int kJacobiMaxSweeps = 40;
+int jacobi_max_sweeps();
 
 }  // namespace wp

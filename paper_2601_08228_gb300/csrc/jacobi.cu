@@ -41,6 +41,8 @@
 // GB300 the FP64 pipe is ~64x slower than FP32, and the angle, being
 // computed from FP32 inputs, gains nothing measurable from FP64.
 
+#include <atomic>
+
 #include "common.cuh"
 #include "internal.cuh"
 #include "jacobi_common.cuh"
@@ -350,7 +352,7 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
   a.vec_out = vec_out;
   a.sig_out = sig_out;
   a.tol = 2.f * sqrtf(float(std::max(a.m_len, 16))) * 1.1920929e-7f;
-  a.max_sweeps = 40;
+  a.max_sweeps = jacobi_max_sweeps();
   a.status = device_status_ptr();
   a.stats = jacobi_stats_ptr();
   // block-cyclic register-resident kernel where the slice shape suits it
@@ -371,6 +373,9 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
 }
 
 static __device__ unsigned long long g_jacobi_stats[2];
+static std::atomic<int> g_jacobi_max_sweeps{kJacobiMaxSweeps};
+
+int jacobi_max_sweeps() { return g_jacobi_max_sweeps.load(std::memory_order_relaxed); }
 
 unsigned long long* jacobi_stats_ptr() {
   static unsigned long long* cached[64] = {nullptr};
@@ -391,6 +396,12 @@ bool jacobi_supported(int n1, int n2) {
 }
 
 }  // namespace wp
+
+extern "C" int wp_set_jacobi_max_sweeps(int max_sweeps) {
+  if (max_sweeps < 1 || max_sweeps > 1000) return WP_ERR_SHAPE;
+  wp::g_jacobi_max_sweeps.store(max_sweeps, std::memory_order_relaxed);
+  return WP_OK;
+}
 
 extern "C" int wp_jacobi_stats(int64_t* total_sweeps, int* max_sweeps) {
   if (!total_sweeps || !max_sweeps) return WP_ERR_NULL;

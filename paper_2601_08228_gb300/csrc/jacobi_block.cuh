@@ -44,11 +44,12 @@ static __device__ __forceinline__ bool try_wait_cluster(uint32_t bar, uint32_t p
   return ok != 0;
 }
 
-// Bounded wait for the peers' partials; WP_ERR_TIMEOUT after 2 s.
-static __device__ __noinline__ bool wait_peers(uint32_t bar, uint32_t parity, int* status) {
+// Bounded wait for the peers' partials; WP_ERR_TIMEOUT after limit_ns (2 s).
+static __device__ __noinline__ bool wait_peers(uint32_t bar, uint32_t parity, int* status,
+                                               uint64_t limit_ns = ptx::kWaitLimitNs) {
   const uint64_t t0 = ptx::globaltimer();
   while (!try_wait_cluster(bar, parity)) {
-    if (ptx::globaltimer() - t0 > ptx::kWaitLimitNs) {
+    if (ptx::globaltimer() - t0 > limit_ns) {
       report_device_error(status, WP_ERR_TIMEOUT);
       return false;
     }

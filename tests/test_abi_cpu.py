@@ -68,3 +68,13 @@ def test_host_validation_needs_no_gpu(libwprod):
     assert L.wp_wprod_host(None, fake, fake, 4, 4, 4, 16, 3, 0, 8, fake, 1 << 20, None) == 1
     assert L.wp_wprod_host(fake, ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), 4, 4, 4, 16, 3, 0, 8,
                            ctypes.c_void_p(4 << 20), 16, None) == 7           # workspace too small
+
+
+def test_limits_validated_on_the_host(libwprod):
+    L = libwprod
+    assert L.wp_set_jacobi_max_sweeps(0) == 2              # WP_ERR_SHAPE, limit unchanged
+    assert L.wp_set_jacobi_max_sweeps(1001) == 2
+    assert L.wp_set_jacobi_max_sweeps(40) == 0             # the default
+    assert L.wp_selftest_bounded_wait(2, 1000000, None) == 2      # unknown wait kind
+    assert L.wp_selftest_bounded_wait(0, 999, None) == 2          # limit below 1 us
+    assert L.wp_selftest_bounded_wait(1, 100000001, None) == 2    # limit above 0.1 s

@@ -26,9 +26,15 @@ def test_peak_and_work_formulas(bench):
     assert bench.wprod_flops() == 2.0 * 256 ** 3 * 192
 
 
-def test_traffic_table_follows_the_source_hash(bench, monkeypatch):
-    val = bench.ncu_traffic("jacobi_svd")
-    assert val is not None and val > 0
+def test_traffic_table_follows_the_source_hash(bench, monkeypatch, tmp_path):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "ncu_traffic.md").write_text(
+        "| kernel | source | source_sha16 | dram_bytes_per_launch |\n|---|---|---|---|\n"
+        "| jacobi_svd | jacobi_block.cuh | 1234abcd5678ef90 | 31760000 |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "_src_hash", lambda fname: "1234abcd5678ef90")
+    assert bench.ncu_traffic("jacobi_svd") == 31760000.0
     assert bench.ncu_traffic("no_such_kernel") is None
     monkeypatch.setattr(bench, "_src_hash", lambda fname: "0000000000000000")
     assert bench.ncu_traffic("jacobi_svd") is None       # source changed: no stale counters

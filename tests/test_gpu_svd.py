@@ -162,7 +162,7 @@ def test_wpinv_remark_2_2():
     np.testing.assert_allclose(O.wprod(Bd, Ad, 1), rem["D"], atol=0.005)
 
 
-PINV_CASES = [(8, 12, 7, 3), (8, 7, 12, 3), (24, 30, 22, 3), (16, 64, 40, 4), (4, 1, 6, 2)]
+PINV_CASES = [(8, 12, 7, 3), (8, 7, 12, 3), (24, 30, 22, 3), (24, 30, 30, 3), (16, 64, 40, 4), (4, 1, 6, 2)]
 
 
 def _kappa(A, L):
@@ -218,3 +218,40 @@ def test_wpinv_invertible_gives_identity():
     tol = max(1e-5, 8 * _kappa(A, L) * 1.2e-7)
     assert O.rel_fro(O.wprod(A, X, L), O.identity(n, p, L)) <= tol
     assert capi.wp_get_device_error() == 0
+
+
+# ---- failure detection: sweep limit and bounded waits ---------------------------
+
+@pytest.mark.parametrize("p,n1,n2,L,r", [(8, 40, 24, 3, 5), (4, 150, 130, 2, 10)])
+def test_jacobi_sweep_limit_reports_not_converged(p, n1, n2, L, r):
+    """With the sweep limit at 1 the Jacobi iteration on random slices cannot
+    converge: the kernels must stop after one sweep and report
+    WP_ERR_NOT_CONVERGED through the device status word (the narrow slices
+    run the shared-memory kernel, the wide ones the block-cyclic kernel)."""
+    A = dev(rand((p, n1, n2), 31))
+    assert capi.wp_get_device_error() == capi.WP_OK
+    capi.wp_set_jacobi_max_sweeps(1)
+    try:
+        capi.wp_wsvd(A, L, r)
+        assert capi.wp_get_device_error() == capi.WP_ERR_NOT_CONVERGED
+    finally:
+        capi.wp_set_jacobi_max_sweeps(40)
+    # back at the default limit the same call converges and matches the oracle
+    Cr = host(capi.wp_wsvd(A, L, r))
+    assert capi.wp_get_device_error() == capi.WP_OK
+    ref = O.wsvd(host(A), L, r)
+    assert O.rel_fro(Cr, ref) <= _rec_tol(host(A), L, r, p)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_wait_expiry_reports_timeout(which):
+    """A bounded wait on a barrier that nothing completes expires after 1 ms,
+    records WP_ERR_TIMEOUT and returns: the context stays usable and the
+    status word is cleared by the read."""
+    assert capi.wp_get_device_error() == capi.WP_OK
+    capi.wp_selftest_bounded_wait(which, 1_000_000)
+    assert capi.wp_get_device_error() == capi.WP_ERR_TIMEOUT
+    assert capi.wp_get_device_error() == capi.WP_OK
+    A, B = rand((8, 16, 12), 1), rand((8, 12, 10), 2)
+    C = host(capi.wp_wprod(dev(A), dev(B), 3))
+    assert O.rel_fro(C, O.wprod(A, B, 3)) <= 1e-5

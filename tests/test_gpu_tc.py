@@ -131,9 +131,9 @@ FUSED_CASES = [
     (16, 1, 1, 1, 4),           # degenerate
     (32, 64, 64, 300, 4),       # wide output: the wide-tile GEMM + separate inverse lift
     (16, 96, 72, 256, 3),       # wide-tile persistent GEMM (MN-major B) + separate inverse lift
-    (16, 96, 48, 256, 3),       # short K: fused, 4 N tiles, A multicast over a 4-CTA cluster
-    (8, 160, 64, 200, 2),       # 2 ragged N tiles of 128: 2-CTA cluster, MN-major B in two 64-column blocks
-    (4, 300, 128, 512, 1),      # BN = 256 (four 64-column B blocks), 3 M tiles, 2-CTA cluster
+    (16, 96, 48, 256, 3),       # short K: fused, 4 N tiles re-reading the A tiles through L2
+    (8, 160, 64, 200, 2),       # 2 ragged N tiles of 128, MN-major B in two 64-column blocks
+    (4, 300, 128, 512, 1),      # BN = 256 (four 64-column B blocks), 3 M tiles
 ]
 
 
