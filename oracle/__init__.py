@@ -26,10 +26,15 @@ Modules:
              gradient-descent objective ||K *w X - Y||^2 + lam||X||^2
   metrics    relative Frobenius error, PSNR (Sec. IV-A)
   quant      emulation of the FP8 (E4M3, one scale per slice) face-product
+  glifting   lifting with general per-level predict / update operators
+             (Eq. 2-3 with arbitrary P_j, U_j; Example 2.1, Remark 3.1), its
+             adjoints, the w-product and gradient built on it
 
 Pinned by tests/test_oracle_*.py against the paper's worked examples
 (Example 2.2, Remark 2.2), closed forms and invariants; the E4M3 rounding of
-`quant` against the format's own value table and PyTorch's float8_e4m3fn.  Nothing here is
+`quant` against the format's own value table and PyTorch's float8_e4m3fn;
+`glifting` against the Haar oracle (its lazy-Haar case), perfect
+reconstruction, its dense block-matrix form and brute-force probing.  Nothing here is
 "parity unpinned".
 """
 
@@ -42,10 +47,11 @@ from .grad import wprod_grad
 from .deblur import deblur_loss, deblur_grad, deblur_steps, deblur_pinv
 from .metrics import rel_fro, psnr
 from .quant import e4m3_round, facewise_fp8, wprod_fp8
+from . import glifting
 
 __all__ = [
     "lift", "ilift", "lift_adjoint", "ilift_adjoint", "split_mallat", "check_levels",
     "dense_lifting_matrix", "facewise", "wprod", "transpose", "identity", "trace",
     "wsvd", "spwsvd", "wpinv", "wprod_grad", "deblur_loss", "deblur_grad",
-    "deblur_steps", "deblur_pinv", "rel_fro", "psnr", "e4m3_round", "facewise_fp8", "wprod_fp8",
+    "deblur_steps", "deblur_pinv", "rel_fro", "psnr", "e4m3_round", "facewise_fp8", "wprod_fp8", "glifting",
 ]
