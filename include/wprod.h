@@ -184,6 +184,93 @@ WP_API int wp_wprod(const float* A, const float* B, float* C, int64_t n1, int64_
              int64_t p, int L, int transA, int transB, int prec, void* ws, size_t ws_bytes,
              void* stream);
 
+/* ---- general predict / update operators (Eq. 2-3, Example 2.1, Remark 3.1) */
+
+/* One level's lifting operators.  Level j splits its input f (length n) into
+ * odd[k] = f[2k] and even[k] = f[2k+1] (0-based storage of Algorithm 1's
+ * 1-based odd / even positions) and computes (Eq. 2)
+ *     d_j = odd - P_j(even),    s_j = even + U_j(d_j)
+ * with stencil operators (Op y)[k] = sum_{t < taps} c_t y[k + offset + t],
+ * 0 <= taps <= 4 (taps = 0: the zero operator), under half-sample symmetric
+ * extension at both ends of the length-n/2 sequence: y[-1-i] = y[i],
+ * y[n/2 + i] = y[n/2 - 1 - i]; every tap must reach less than n/2 positions
+ * from k (else WP_ERR_SHAPE).  P = {0, 1, {1}}, U = {0, 1, {0.5}} is the
+ * lazy-Haar transform of wp_lift_forward; Example 2.1's interpolating
+ * predict is P = {-1, 2, {0.5, 0.5}} with U = 0. */
+typedef struct {
+  int32_t predict_offset;
+  int32_t predict_taps;
+  float predict[4];
+  int32_t update_offset;
+  int32_t update_taps;
+  float update[4];
+} wp_lift_ops;
+
+/* Transform every mode-3 tube of x (p, n1, n2) with the L levels' operators
+ * ops[0..L) (host array): op = 0 forward W (Mallat order out, Eq. 1),
+ * 1 inverse W^{-1} (Eq. 3; Mallat order in), 2 the adjoint W^T (Mallat order
+ * in), 3 W^{-T} (Mallat order out).  All levels in one pass over HBM; one
+ * thread per tube holds the whole tube in shared memory, so p <= 800
+ * (WP_ERR_UNSUPPORTED beyond).  x and y must not overlap. */
+WP_API int wp_glift(const float* x, float* y, int64_t n1, int64_t n2, int64_t p, int L,
+                    const wp_lift_ops* ops, int op, void* stream);
+
+/* C = W^{-1}( W(A) Delta W(B) ) (Def. 2.1) with the general operators:
+ * A (p, n1, n2), B (p, n2, n4), C (p, n1, n4); face-products in `prec`. */
+WP_API int wp_gwprod_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
+                               size_t* bytes);
+WP_API int wp_gwprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
+                     int64_t p, int L, const wp_lift_ops* ops, int prec, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* Backward of wp_gwprod by the adjoint route (the transform is not
+ * orthogonal): G_hat = W^{-T} G, dA = W^T (G_hat Delta B_hat^T),
+ * dB = W^T (A_hat^T Delta G_hat); dA or dB may be NULL. */
+WP_API int wp_gwprod_backward_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
+                                        size_t* bytes);
+WP_API int wp_gwprod_backward(const float* A, const float* B, const float* G, float* dA, float* dB,
+                              int64_t n1, int64_t n2, int64_t n4, int64_t p, int L,
+                              const wp_lift_ops* ops, int prec, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* ---- autotuner and plan cache of the tensor-core w-product -------------- */
+
+/* The BF16 / BF16X3 w-product without transposes (1 <= L <= 5) has two
+ * kernels: (1) one CTA per 128 x (512 / 2^L) tile of all 2^L slices of a
+ * tube group, whose epilogue applies the inverse lift (Eq. 3) across the 2^L
+ * tensor-memory accumulators, so the wavelet-domain product never reaches
+ * HBM; (2) a persistent wide-tile GEMM into the wavelet-domain product, then
+ * a separate inverse lift.  Both compute the same product (Algorithm 1); the
+ * faster depends on the shape.  wp_wprod takes the variant stored for the
+ * shape in a process-wide plan cache keyed by (n1, n2, n4, p, L, prec), else
+ * a rule of thumb measured on GB300.
+ *
+ * wp_wprod_tune: times both variants on the caller's tensors (one warm-up
+ * call, then the mean of three back-to-back calls each, CUDA events on
+ * `stream`), stores the faster in the cache and returns it in *variant
+ * (1 fused epilogue, 2 persistent GEMM + inverse lift) and its time in
+ * *best_ms (if not NULL).  C holds the product on return.  Synchronises
+ * `stream`; do not call it while the stream is being captured.  For
+ * arguments with a single kernel (FP32, FP8, transposes, L = 0 or L > 5) it
+ * runs wp_wprod once and returns WP_OK with *variant = 0.
+ * wp_plan_set: stores variant 1 or 2 for the key; <= 0 removes the entry.
+ * wp_plan_get: *variant = the cached value, 0 if none.
+ * wp_plan_clear: empties the cache.
+ * wp_plan_save / wp_plan_load: write / read the cache as a text file of one
+ *   JSON object per line ({"op": "wprod", "n1": .., "n2": .., "n4": .., "p":
+ *   .., "L": .., "prec": .., "variant": .., "ms": ..}); load adds the file's
+ *   entries to the cache (*entries = how many, if not NULL) and returns
+ *   WP_ERR_SHAPE for an unreadable file or a malformed line (the entries
+ *   before it are kept). */
+WP_API int wp_wprod_tune(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
+                         int64_t p, int L, int prec, void* ws, size_t ws_bytes, void* stream,
+                         int* variant, double* best_ms);
+WP_API int wp_plan_set(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec, int variant);
+WP_API int wp_plan_get(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec, int* variant);
+WP_API int wp_plan_clear(void);
+WP_API int wp_plan_save(const char* path);
+WP_API int wp_plan_load(const char* path, int* entries);
+
 /* ---- w-product of host-resident tensors ---------------------------------- */
 
 /* C = A *w B (Def. 2.1, Algorithm 1; no transposes) for A (p, n1, n2),
@@ -356,8 +443,14 @@ typedef struct {
  * final until wp_batched_run).  wp_batched_run launches the four phases
  * (lifting, face-products, Jacobi SVD with rank-r rebuild, inverse lifting;
  * the Jacobi phase as up to three launches, one per slice-width class of the
- * plan); it neither allocates, copies nor synchronises, so it can be
- * captured in a CUDA graph and replayed while the workspace and the items'
+ * plan).  The face-products run on a library-owned second stream of the
+ * device (created on the first call), forked from `stream` after the lifting
+ * and joined back before the inverse lifting, so they overlap the Jacobi
+ * phase; calls on one device therefore share that stream and must not run
+ * concurrently from several host threads.  The call neither allocates,
+ * copies nor synchronises, so it can be captured in a CUDA graph (the fork
+ * and join become graph dependencies; wp_batched_plan creates the second
+ * stream beforehand) and replayed while the workspace and the items'
  * buffers live. */
 WP_API int wp_batched_workspace(const wp_batch_item* items, int count, size_t* bytes);
 WP_API int wp_batched_plan(const wp_batch_item* items, int count, int tune, void* ws, size_t ws_bytes,

@@ -51,6 +51,12 @@ class WPBatchPlan(ctypes.Structure):
                 ("units_off", ctypes.c_uint64)]
 
 
+class WPLiftOps(ctypes.Structure):
+    _fields_ = [("predict_offset", ctypes.c_int32), ("predict_taps", ctypes.c_int32),
+                ("predict", ctypes.c_float * 4), ("update_offset", ctypes.c_int32),
+                ("update_taps", ctypes.c_int32), ("update", ctypes.c_float * 4)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I = ctypes.c_int
@@ -64,6 +70,19 @@ _SIGNATURES = {
     "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
     "wp_set_jacobi_max_sweeps": ([_I], _I),
     "wp_selftest_bounded_wait": ([_I, _I64, _P], _I),
+    "wp_wprod_tune": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P, ctypes.POINTER(_I),
+                       ctypes.POINTER(ctypes.c_double)], _I),
+    "wp_glift": ([_P, _P, _I64, _I64, _I64, _I, ctypes.POINTER(WPLiftOps), _I, _P], _I),
+    "wp_gwprod_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_gwprod": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, ctypes.POINTER(WPLiftOps), _I, _P, _SZ, _P], _I),
+    "wp_gwprod_backward_workspace": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "wp_gwprod_backward": ([_P, _P, _P, _P, _P, _I64, _I64, _I64, _I64, _I, ctypes.POINTER(WPLiftOps), _I, _P,
+                            _SZ, _P], _I),
+    "wp_plan_set": ([_I64, _I64, _I64, _I64, _I, _I, _I], _I),
+    "wp_plan_get": ([_I64, _I64, _I64, _I64, _I, _I, ctypes.POINTER(_I)], _I),
+    "wp_plan_clear": ([], _I),
+    "wp_plan_save": ([ctypes.c_char_p], _I),
+    "wp_plan_load": ([ctypes.c_char_p, ctypes.POINTER(_I)], _I),
     "wp_deblur_pinv_workspace": ([_I64, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "wp_deblur_pinv": ([_P, _P, _P, _P, _I64, _I64, _I64, _I, ctypes.c_double, _I, _I, _P, _SZ, _P], _I),
     "wp_profile_begin": ([], _I),
@@ -210,6 +229,106 @@ def wp_wprod(A, B, L, transA=False, transB=False, prec="fp32", out=None, ws=None
     _check(lib().wp_wprod(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, int(transA), int(transB), pr,
                           _ptr(ws), ws.numel(), _stream()), "wp_wprod")
     return C
+
+
+GLIFT_OPS = {"forward": 0, "inverse": 1, "adjoint": 2, "inverse_adjoint": 3}
+
+
+def lift_ops(levels):
+    """ctypes array of wp_lift_ops from [((p_off, p_taps), (u_off, u_taps)), ...]."""
+    arr = (WPLiftOps * max(1, len(levels)))()
+    for j, ((po, pt), (uo, ut)) in enumerate(levels):
+        if len(pt) > 4 or len(ut) > 4:
+            raise ValueError("at most 4 taps per operator")
+        arr[j].predict_offset, arr[j].predict_taps = int(po), len(pt)
+        arr[j].update_offset, arr[j].update_taps = int(uo), len(ut)
+        for t, c in enumerate(pt):
+            arr[j].predict[t] = float(c)
+        for t, c in enumerate(ut):
+            arr[j].update[t] = float(c)
+    return arr
+
+
+def wp_glift(x, L, levels, op="forward", out=None):
+    """General-operator lifting of every mode-3 tube (see include/wprod.h)."""
+    _req(x, "x")
+    p, n1, n2 = x.shape
+    y = torch.empty_like(x) if out is None else _req(out, "out")
+    _check(lib().wp_glift(_ptr(x), _ptr(y), n1, n2, p, L, lift_ops(levels), GLIFT_OPS[op], _stream()), "wp_glift")
+    return y
+
+
+def wp_gwprod(A, B, L, levels, prec="fp32", out=None):
+    _req(A, "A"), _req(B, "B")
+    p, n1, n2, n4 = _prod_dims(A, B, False, False)
+    pr = _prec(prec)
+    n = _SZ(0)
+    _check(lib().wp_gwprod_workspace(n1, n2, n4, p, L, pr, ctypes.byref(n)), "wp_gwprod_workspace")
+    ws = _workspace(n.value, A.device)
+    C = torch.empty((p, n1, n4), dtype=torch.float32, device=A.device) if out is None else _req(out, "out")
+    _check(lib().wp_gwprod(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, lift_ops(levels), pr, _ptr(ws), ws.numel(),
+                           _stream()), "wp_gwprod")
+    return C
+
+
+def wp_gwprod_backward(A, B, G, L, levels, prec="fp32", need_dA=True, need_dB=True):
+    _req(A, "A"), _req(B, "B"), _req(G, "G")
+    p, n1, n2, n4 = _prod_dims(A, B, False, False)
+    pr = _prec(prec)
+    n = _SZ(0)
+    _check(lib().wp_gwprod_backward_workspace(n1, n2, n4, p, L, pr, ctypes.byref(n)), "wp_gwprod_backward_workspace")
+    ws = _workspace(n.value, A.device)
+    dA = torch.empty_like(A) if need_dA else None
+    dB = torch.empty_like(B) if need_dB else None
+    _check(lib().wp_gwprod_backward(_ptr(A), _ptr(B), _ptr(G), _ptr(dA) if dA is not None else None,
+                                    _ptr(dB) if dB is not None else None, n1, n2, n4, p, L, lift_ops(levels), pr,
+                                    _ptr(ws), ws.numel(), _stream()), "wp_gwprod_backward")
+    return dA, dB
+
+
+WPROD_VARIANTS = {"fused": 1, "persistent": 2}
+
+
+def wp_wprod_tune(A, B, L, prec="bf16x3", out=None, ws=None):
+    """Time both tensor-core w-product kernels on these tensors and cache the
+    faster; returns (variant, best_ms): 1 fused inverse-lift epilogue, 2
+    persistent GEMM + inverse lift; (0, 0.0) when there is only one kernel."""
+    _req(A, "A"), _req(B, "B")
+    p, n1, n2, n4 = _prod_dims(A, B, False, False)
+    pr = _prec(prec)
+    need = wp_wprod_workspace(n1, n2, n4, p, L, pr)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, A.device)
+    C = torch.empty((p, n1, n4), dtype=torch.float32, device=A.device) if out is None else _req(out, "out")
+    cg, ms = _I(0), ctypes.c_double(0.0)
+    _check(lib().wp_wprod_tune(_ptr(A), _ptr(B), _ptr(C), n1, n2, n4, p, L, pr, _ptr(ws), ws.numel(), _stream(),
+                               ctypes.byref(cg), ctypes.byref(ms)), "wp_wprod_tune")
+    return int(cg.value), float(ms.value)
+
+
+def wp_plan_set(n1, n2, n4, p, L, prec, variant):
+    v = WPROD_VARIANTS.get(variant, variant) if isinstance(variant, str) else variant
+    _check(lib().wp_plan_set(n1, n2, n4, p, L, _prec(prec), int(v)), "wp_plan_set")
+
+
+def wp_plan_get(n1, n2, n4, p, L, prec):
+    v = _I(0)
+    _check(lib().wp_plan_get(n1, n2, n4, p, L, _prec(prec), ctypes.byref(v)), "wp_plan_get")
+    return int(v.value)
+
+
+def wp_plan_clear():
+    _check(lib().wp_plan_clear(), "wp_plan_clear")
+
+
+def wp_plan_save(path):
+    _check(lib().wp_plan_save(os.fsencode(path)), "wp_plan_save")
+
+
+def wp_plan_load(path):
+    n = _I(0)
+    _check(lib().wp_plan_load(os.fsencode(path), ctypes.byref(n)), "wp_plan_load")
+    return int(n.value)
 
 
 def _req_host(t, name):

@@ -22,6 +22,8 @@
 
 #include <vector>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.cuh"
 #include "jacobi_block.cuh"
@@ -442,9 +444,37 @@ extern "C" int wp_batched_workspace(const wp_batch_item* items, int count, size_
   return WP_OK;
 }
 
+// Second stream and fork / join events of one device (created on first use,
+// kept for the life of the process): the face-product phase runs on it beside
+// the Jacobi phases, which do not depend on it.
+struct BatchFork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool ok = false;
+};
+
+static BatchFork* batch_fork() {
+  static std::mutex mu;
+  static BatchFork forks[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  BatchFork& f = forks[dev];
+  if (!f.ok) {
+    if (cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) != cudaSuccess)
+      return nullptr;
+    f.ok = true;
+  }
+  return &f;
+}
+
 extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, void* ws, size_t ws_bytes,
                                wp_batch_plan* plan, void* stream) {
   if (!plan) return WP_ERR_NULL;
+  // the run's second stream exists before any capture of wp_batched_run
+  if (!batch_fork()) return WP_ERR_CUDA;
   WP_TRY(validate_items(items, count));
   BatchLayout lay;
   batch_layout(items, count, lay);
@@ -536,14 +566,22 @@ extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream)
   cudaStream_t st = as_stream(stream);
   const BItem* di = reinterpret_cast<const BItem*>(base + plan->items_off);
   const int2* du = reinterpret_cast<const int2*>(base + plan->units_off);
+  BatchFork* f = batch_fork();
+  if (!f) return WP_ERR_CUDA;
   WP_TRY(launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_fwd_off), plan->n_lift_fwd,
                              plan->lift_fwd_blocks, st));
-  WP_TRY(launch_batched_gemm(di, du, plan->n_units, plan->gemm_threads, st));
+  // the face-products (C_hat) and the Jacobi phases (C_r_hat) both read only
+  // the lifted operands: the face-products go to the side stream
+  WP_CUDA_TRY(cudaEventRecord(f->fork, st));
+  WP_CUDA_TRY(cudaStreamWaitEvent(f->side, f->fork, 0));
+  WP_TRY(launch_batched_gemm(di, du, plan->n_units, plan->gemm_threads, f->side));
   const int64_t nn = plan->n_units_narrow, nm = plan->n_units_mid;
   WP_TRY(launch_batched_jacobi_narrow(di, du, nn, plan->svd_vec_floats, st));
   WP_TRY(launch_batched_jacobi_mid(di, du + nn, nm, plan->svd_vec_floats, st));
   WP_TRY(launch_batched_jacobi(di, du + nn + nm, plan->n_units - nn - nm, plan->svd_threads, plan->svd_vec_floats,
                                st));
+  WP_CUDA_TRY(cudaEventRecord(f->join, f->side));
+  WP_CUDA_TRY(cudaStreamWaitEvent(st, f->join, 0));
   return launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_inv_off), plan->n_lift_inv,
                              plan->lift_inv_blocks, st);
 }

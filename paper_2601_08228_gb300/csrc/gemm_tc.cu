@@ -1456,14 +1456,43 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
   return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st, true);
 }
 
+// Which of the two BF16 / BF16x3 w-product kernels a shape takes.  The
+// inverse-lift epilogue needs all 2^L accumulators of a tile in TMEM, so its
+// tile is only 512 / 2^L wide.  Rule of thumb, measured on GB300 (BF16x3,
+// the 256 x 256 x 192 L = 3 case and neighbours): the fused kernel wins with
+// wide tiles (L <= 2), short K (n2 <= 64, where the wavelet-domain round trip
+// of C dominates) and small slices (n1, n4 <= 128); otherwise the persistent
+// wide-tile GEMM into C_hat plus a separate inverse lift is faster (88 vs
+// 96 us at 256 x 256 x 192).  A choice timed by wp_wprod_tune for the shape
+// (plan cache, tune.cu) takes precedence: 1 fused, 2 persistent + inverse lift.
+static bool fused_rule(int64_t n1, int64_t n2, int64_t n4, int L) {
+  const int64_t bn_fused = 512 >> L;
+  return (n4 + bn_fused - 1) / bn_fused <= 4 && (L <= 2 || n2 <= 64 || (n1 <= 128 && n4 <= 128));
+}
+
+static bool use_epilogue_fused(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec) {
+  const int v = wprod_plan_lookup(n1, n2, n4, p, L, prec);
+  if (v == kVariantFused) return true;
+  if (v == kVariantPersistent) return false;
+  return fused_rule(n1, n2, n4, L);
+}
+
+static bool fused_domain(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec) {
+  if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3 && prec != WP_PREC_FP8) return false;
+  if (L < 1 || L > 5) return false;
+  return !((p >> L) > 65535 || p > 65535 || n1 > INT32_MAX || n2 > INT32_MAX || n4 > INT32_MAX);
+}
+
+bool wprod_tunable(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec) {
+  return (prec == WP_PREC_BF16 || prec == WP_PREC_BF16X3) && fused_domain(n1, n2, n4, p, L, prec);
+}
+
 // C = A *w B for tensor-core precisions with the transform fused into the
 // operand preparation and the GEMM epilogue.  WP_ERR_UNSUPPORTED when the
 // arguments fall outside the fused path (the caller then uses the unfused one).
 int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p, int L,
                    int prec, void* ws, size_t ws_bytes, cudaStream_t st) {
-  if (prec != WP_PREC_BF16 && prec != WP_PREC_BF16X3 && prec != WP_PREC_FP8) return WP_ERR_UNSUPPORTED;
-  if (L < 1 || L > 5) return WP_ERR_UNSUPPORTED;
-  if ((p >> L) > 65535 || p > 65535 || n1 > INT32_MAX || n2 > INT32_MAX || n4 > INT32_MAX) return WP_ERR_UNSUPPORTED;
+  if (!fused_domain(n1, n2, n4, p, L, prec)) return WP_ERR_UNSUPPORTED;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return WP_ERR_ALIGN;
   if (prec == WP_PREC_FP8) {
     if (2 * (p >> L) > 65535) return WP_ERR_UNSUPPORTED;
@@ -1477,17 +1506,7 @@ int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t
   }
   const int64_t Kp = pad8(n2);
   const bool x3 = (prec == WP_PREC_BF16X3);
-  // The inverse-lift epilogue needs all 2^L accumulators of a tile in TMEM,
-  // so its tile is only 512 / 2^L wide.  Measured on GB300 (BF16x3, the
-  // 256 x 256 x 192 L = 3 case and neighbours): the fused kernel wins with
-  // wide tiles (L <= 2), short K (n2 <= 64, where the wavelet-domain round
-  // trip of C dominates) and small slices (n1, n4 <= 128); otherwise the
-  // persistent wide-tile GEMM into C_hat plus a separate inverse lift is
-  // faster (88 vs 96 us at 256 x 256 x 192), and it is the only choice when
-  // the fused tile would re-read A more than four times.
-  const int64_t bn_fused = 512 >> L;
-  const bool epilogue_fused = (n4 + bn_fused - 1) / bn_fused <= 4 &&
-                              (L <= 2 || n2 <= 64 || (n1 <= 128 && n4 <= 128));
+  const bool epilogue_fused = use_epilogue_fused(n1, n2, n4, p, L, prec);
   Carver cv(ws, ws_bytes);
   float* Chat = epilogue_fused ? nullptr : cv.take<float>(size_t(p) * n1 * n4);
   // B operand: (p, n2, pad8(n4)) MN-major on the fused-epilogue path at

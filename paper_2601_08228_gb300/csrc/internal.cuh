@@ -29,6 +29,13 @@ int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, 
 // WP_ERR_UNSUPPORTED outside its domain (no transposes, 1 <= L <= 5).
 int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
                    int64_t p, int L, int prec, void* ws, size_t ws_bytes, cudaStream_t st);
+// True when wp_wprod (no transposes) has two tensor-core kernels to choose
+// from for these arguments: the fused inverse-lift epilogue kernel, or the
+// persistent GEMM into C_hat plus a separate inverse lift.
+bool wprod_tunable(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec);
+constexpr int kVariantFused = 1, kVariantPersistent = 2;
+// The tuned variant for this shape (tune.cu); 0 if none.
+int wprod_plan_lookup(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec);
 
 }  // namespace wp
 
@@ -38,9 +45,18 @@ namespace wp {
 // slices [slice0, slice0 + nslices) of X (p, n1, n2).  vec_out (p, max(n1,n2), r)
 // receives unit left vectors when n1 >= n2, unit right vectors otherwise;
 // sig_out (p, r) the singular values in descending order.
+// Slices too large for a thread-block cluster's shared memory run on the
+// global-memory kernel (jacobi_global.cu), which needs `work` of
+// jacobi_work_bytes(n1, n2, nslices) bytes (0 for every other shape).
 int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, float* vec_out, float* sig_out,
-               cudaStream_t st);
+               cudaStream_t st, void* work = nullptr, size_t work_bytes = 0);
 bool jacobi_supported(int n1, int n2);
+size_t jacobi_work_bytes(int n1, int n2, int nslices);
+// global-memory kernel (jacobi_global.cu)
+size_t jacobi_global_work_bytes(int n1, int n2, int nslices);
+bool jacobi_global_supported(int n1, int n2);
+struct JacobiArgs;
+int jacobi_global_launch(const JacobiArgs& a, int nslices, void* work, size_t work_bytes, cudaStream_t st);
 // Device address of the Jacobi sweep counters ([0] total slice-sweeps, [1] max).
 unsigned long long* jacobi_stats_ptr();
 // Sweep limit passed to every Jacobi launch (default kJacobiMaxSweeps; set by

@@ -336,7 +336,7 @@ static int launch_jacobi_lg(const JacobiArgs& args, int nslices, size_t smem, cu
 // (p, n1, n2).  Writes unit vectors (p, max(n1,n2), r) -- left vectors when
 // n1 >= n2, right vectors otherwise -- and singular values (p, r).
 int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, float* vec_out, float* sig_out,
-               cudaStream_t st) {
+               cudaStream_t st, void* work, size_t work_bytes) {
   if (nslices <= 0) return WP_OK;
   JacobiArgs a{};
   a.X = X;
@@ -361,7 +361,7 @@ int jacobi_svd(const float* X, int n1, int n2, int slice0, int nslices, int r, f
     if (rc != WP_ERR_UNSUPPORTED) return rc;
   }
   const int CL = pick_cluster(a.m_len, a.n_pad, nslices);
-  if (CL < 0) return WP_ERR_UNSUPPORTED;
+  if (CL < 0) return jacobi_global_launch(a, nslices, work, work_bytes, st);
   a.rpc = (a.m_len + CL - 1) / CL;
   const size_t smem = jacobi_smem(a.n_pad, a.rpc, CL);
   switch (CL) {
@@ -389,10 +389,18 @@ unsigned long long* jacobi_stats_ptr() {
   return cached[dev];
 }
 
-bool jacobi_supported(int n1, int n2) {
+// The cluster kernels take the slice when it fits in the shared memory of an
+// 8-CTA cluster (the block-cyclic kernel's register shapes are a subset).
+static bool cluster_fits(int n1, int n2) {
   const int m_len = std::max(n1, n2), n_vec = std::min(n1, n2);
   const int n_pad = std::max(2, n_vec + (n_vec & 1));
   return pick_cluster(m_len, n_pad, 1) > 0;
+}
+
+bool jacobi_supported(int n1, int n2) { return cluster_fits(n1, n2) || jacobi_global_supported(n1, n2); }
+
+size_t jacobi_work_bytes(int n1, int n2, int nslices) {
+  return cluster_fits(n1, n2) ? 0 : jacobi_global_work_bytes(n1, n2, nslices);
 }
 
 }  // namespace wp

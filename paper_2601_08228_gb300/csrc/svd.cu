@@ -158,6 +158,7 @@ static void wsvd_layout(int64_t n1, int64_t n2, int64_t p, int r, Sizer& s) {
   s.take<float>(size_t(p) * n1 * r);    // spatial-domain factor staging: U
   s.take<float>(size_t(p) * r);         //                              S
   s.take<float>(size_t(p) * n2 * r);    //                              V
+  s.take<char>(jacobi_work_bytes(int(n1), int(n2), int(p)));   // large slices: Jacobi work buffer
 }
 
 static int check_wsvd(int64_t n1, int64_t n2, int64_t p, int L, int r) {
@@ -209,6 +210,8 @@ extern "C" int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V,
   float* Uw = cv.take<float>(size_t(p) * n1 * r);
   float* Sw = cv.take<float>(size_t(p) * r);
   float* Vw = cv.take<float>(size_t(p) * n2 * r);
+  const size_t jw = jacobi_work_bytes(int(n1), int(n2), int(p));
+  void* jwork = jw ? cv.take<char>(jw) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
   const int N1 = int(n1), N2 = int(n2);
@@ -217,7 +220,7 @@ extern "C" int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V,
   const bool trans = n1 < n2;
 
   WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, n1 * n2, p, L, st));
-  WP_TRY(jacobi_svd(Ah, N1, N2, 0, nsl, r, vec, sig, st));
+  WP_TRY(jacobi_svd(Ah, N1, N2, 0, nsl, r, vec, sig, st, jwork, jw));
   if (!trans) {
     // T = U_r^T A_hat (r x n2), C_hat = U_r T
     WP_TRY(sgemm_batched(vec, Ah, T, r, N2, N1, true, false, nsl, st));
@@ -262,6 +265,7 @@ static void wpinv_layout(int64_t m, int64_t n, int64_t p, Sizer& s) {
   s.take<float>(size_t(p) * n * m);     // X_hat
   s.take<float>(size_t(p) * m * m);     // residual R
   s.take<float>(size_t(p) * n * m);     // X R
+  s.take<char>(jacobi_work_bytes(int(m), int(n), int(p)));   // large slices: Jacobi work buffer
 }
 
 extern "C" int wp_wpinv_workspace(int64_t m, int64_t n, int64_t p, int L, size_t* bytes) {
@@ -297,13 +301,15 @@ extern "C" int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t 
   float* Xh = cv.take<float>(size_t(p) * n * m);
   float* R = cv.take<float>(size_t(p) * m * m);
   float* XR = cv.take<float>(size_t(p) * n * m);
+  const size_t jw = jacobi_work_bytes(int(m), int(n), int(p));
+  void* jwork = jw ? cv.take<char>(jw) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
   const int M = int(m), N = int(n), P = int(p), K = int(mn);
   const float tol = rtol < 0 ? float(mx) * 1.1920929e-7f : float(rtol);
 
   WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, m * n, p, L, st));
-  WP_TRY(jacobi_svd(Ah, M, N, 0, P, K, vec, sig, st));
+  WP_TRY(jacobi_svd(Ah, M, N, 0, P, K, vec, sig, st, jwork, jw));
   if (m >= n) {
     // U = vec (m x n); T = A^T U (n x n); T *= w; X_hat = T U^T (n x m)
     WP_TRY(sgemm_batched(Ah, vec, T, N, N, M, true, false, P, st));

@@ -78,3 +78,38 @@ def test_limits_validated_on_the_host(libwprod):
     assert L.wp_selftest_bounded_wait(2, 1000000, None) == 2      # unknown wait kind
     assert L.wp_selftest_bounded_wait(0, 999, None) == 2          # limit below 1 us
     assert L.wp_selftest_bounded_wait(1, 100000001, None) == 2    # limit above 0.1 s
+
+
+def test_plan_cache_round_trip(libwprod, tmp_path):
+    """The w-product plan cache (host only): set / get / remove, validation,
+    and the JSON-lines file written by wp_plan_save read back by wp_plan_load."""
+    from paper_2601_08228_gb300 import capi
+    capi.wp_plan_clear()
+    capi.wp_plan_set(256, 256, 256, 192, 3, "bf16x3", "persistent")
+    capi.wp_plan_set(64, 32, 48, 16, 2, "bf16", "fused")
+    assert capi.wp_plan_get(256, 256, 256, 192, 3, "bf16x3") == 2
+    assert capi.wp_plan_get(256, 256, 256, 192, 3, "bf16") == 0          # another key
+    with pytest.raises(capi.WPError) as e:
+        capi.wp_plan_set(256, 256, 256, 192, 3, "bf16x3", 3)               # no such variant
+    assert e.value.status == capi.WP_ERR_SHAPE
+    with pytest.raises(capi.WPError) as e:
+        capi.wp_plan_set(256, 256, 256, 12, 3, "bf16x3", 1)               # p % 2^L
+    assert e.value.status == capi.WP_ERR_LEVELS
+    path = tmp_path / "plans.jsonl"
+    capi.wp_plan_save(str(path))
+    lines = path.read_text().splitlines()
+    assert len(lines) == 2 and all('"op": "wprod"' in x and '"variant"' in x for x in lines)
+    capi.wp_plan_clear()
+    assert capi.wp_plan_get(64, 32, 48, 16, 2, "bf16") == 0
+    assert capi.wp_plan_load(str(path)) == 2
+    assert capi.wp_plan_get(64, 32, 48, 16, 2, "bf16") == 1
+    assert capi.wp_plan_get(256, 256, 256, 192, 3, "bf16x3") == 2
+    capi.wp_plan_set(64, 32, 48, 16, 2, "bf16", 0)                        # removes the entry
+    assert capi.wp_plan_get(64, 32, 48, 16, 2, "bf16") == 0
+    bad = tmp_path / "bad.jsonl"
+    bad.write_text('{"op": "wprod", "n1": 4, "n2": 4, "n4": 4, "p": 8, "L": 3, "prec": 2, "variant": 7, "ms": 1}\n')
+    with pytest.raises(capi.WPError):
+        capi.wp_plan_load(str(bad))
+    with pytest.raises(capi.WPError):
+        capi.wp_plan_load(str(tmp_path / "missing.jsonl"))
+    capi.wp_plan_clear()

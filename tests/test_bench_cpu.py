@@ -73,3 +73,15 @@ def test_clock_log_summary(bench, tmp_path):
     summ = cs.summary()
     assert summ["sm_mhz"] == 2070.0 and summ["sm_max_mhz"] == 2070.0 and summ["samples"] == 3
     assert summ["reasons"] == ["sw_power_cap"]
+
+
+def test_median_time_and_oracle_sample(bench):
+    calls = []
+    med, n = bench._median_time(lambda: calls.append(1), 5, 10.0)
+    assert n == 5 and len(calls) == 5 and med >= 0.0
+    # a budget already spent stops after the first call
+    med, n = bench._median_time(lambda: __import__("time").sleep(0.01), 5, 0.0)
+    assert n == 1
+    # the w-svd sample is a whole number of tube groups and scales to the workload
+    w = bench.WORKLOAD
+    assert bench.SAMPLE_P % (1 << w["L"]) == 0 and bench.SAMPLE_P * bench.SAMPLE_SCALE == w["p"]

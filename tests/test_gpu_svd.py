@@ -255,3 +255,49 @@ def test_bounded_wait_expiry_reports_timeout(which):
     A, B = rand((8, 16, 12), 1), rand((8, 12, 10), 2)
     C = host(capi.wp_wprod(dev(A), dev(B), 3))
     assert O.rel_fro(C, O.wprod(A, B, 3)) <= 1e-5
+
+
+# ---- slices larger than a cluster's shared memory (global-memory Jacobi) ---------
+
+BIG_CASES = [
+    # p, n1, n2, L, r   (n1 * n2 > ~400k: beyond the 8-CTA cluster kernels)
+    (2, 640, 640, 1, 12),     # square, 16-column blocks
+    (4, 700, 600, 2, 30),     # tall: left vectors from Jacobi
+    (2, 600, 700, 1, 8),      # wide: the working columns are the slice's rows
+    (2, 1700, 260, 1, 5),     # 1700 rows: 8-column blocks
+]
+
+
+@pytest.mark.parametrize("p,n1,n2,L,r", BIG_CASES)
+def test_wsvd_large_slices(p, n1, n2, L, r):
+    A = rand((p, n1, n2), n1 + n2)
+    C, U, S, V = capi.wp_wsvd(dev(A), L, r, factors=True)
+    Cr, Ur, Sr, Vr = O.wsvd(A, L, r, return_factors=True)
+    assert O.rel_fro(host(S), Sr) <= TOL_SIG
+    assert O.rel_fro(host(C), Cr) <= _rec_tol(A, L, r, p)
+    assert capi.wp_get_device_error() == 0
+
+
+def test_wpinv_large_square_slice():
+    """A 640 x 640 slice pair, inverted through the global-memory Jacobi, then
+    refined: the Penrose equations at the kappa-aware bars."""
+    p, n, L = 2, 640, 1
+    A = rand((p, n, n), 77)
+    X = host(capi.wp_wpinv(dev(A), L, refine_iters=2))
+    kap, eps = _kappa(A, L), 1.2e-7
+    assert O.rel_fro(X, O.wpinv(A, L)) <= max(1e-4, 8 * kap * eps)
+    AX = O.wprod(A, X, L)
+    assert O.rel_fro(O.wprod(AX, A, L), A) <= max(1e-4, 8 * kap * eps)
+    assert capi.wp_get_device_error() == 0
+
+
+def test_wpinv_zero_detail_slices_large():
+    """A band-constant operator (zero detail slices, as the blur operators of
+    Sec. IV-C) with 610 x 610 slices: the zero slices converge at once and
+    their pseudo-inverse is zero; the result matches the oracle."""
+    p, n, L = 4, 610, 1
+    T = np.random.default_rng(5).standard_normal((n, n)).astype(np.float32) + 30 * np.eye(n, dtype=np.float32)
+    A = np.broadcast_to(T, (p, n, n)).copy()
+    X = host(capi.wp_wpinv(dev(A), L, refine_iters=1))
+    assert O.rel_fro(X, O.wpinv(A, L)) <= 1e-4
+    assert capi.wp_get_device_error() == 0

@@ -230,3 +230,48 @@ def test_facewise_and_unfused_wprod_fp8_match_emulation(tA, tB):
     assert O.rel_fro(C, O.facewise_fp8(At, Bt)) <= TOL_FP8_EMU
     C = host(capi.wp_wprod(dev(A), dev(B), L, transA=tA, transB=tB, prec="fp8"))
     assert O.rel_fro(C, O.wprod_fp8(np.ascontiguousarray(At), np.ascontiguousarray(Bt), L)) <= TOL_FP8_EMU
+
+
+VARIANT_CASES = [
+    # p, n1, n2, n4, L: each shape run on both tensor-core w-product kernels
+    (64, 200, 136, 530, 2),     # wide output: the fused kernel's 128-wide tiles re-read A five times
+    (48, 160, 96, 260, 3),
+    (96, 256, 256, 256, 3),     # the benchmark's slice shape
+    (32, 130, 72, 258, 4),      # N not a multiple of 4 (direct stores)
+    (64, 96, 200, 130, 5),      # L = 5, 16-wide fused tiles
+    (8, 64, 40, 64, 3),         # a shape the rule sends to the fused kernel
+]
+
+
+@pytest.mark.parametrize("p,n1,n2,n4,L", VARIANT_CASES)
+@pytest.mark.parametrize("variant", ["fused", "persistent"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_wprod_both_kernels(p, n1, n2, n4, L, variant, prec):
+    """The fused inverse-lift epilogue kernel and the persistent GEMM + inverse
+    lift, forced through the plan cache, both give the w-product."""
+    A, B = rand((p, n1, n2), 21), rand((p, n2, n4), 22)
+    capi.wp_plan_clear()
+    capi.wp_plan_set(n1, n2, n4, p, L, prec, variant)
+    try:
+        C = host(capi.wp_wprod(dev(A), dev(B), L, prec=prec))
+    finally:
+        capi.wp_plan_clear()
+    err = O.rel_fro(C, O.wprod(A, B, L))
+    assert err <= (TOL_X3 if prec == "bf16x3" else TOL_BF16), err
+    assert capi.wp_get_device_error() == 0
+
+
+def test_wprod_tuner():
+    p, n1, n2, n4, L = 64, 256, 192, 256, 3
+    A, B = rand((p, n1, n2), 23), rand((p, n2, n4), 24)
+    Ad, Bd = dev(A), dev(B)
+    capi.wp_plan_clear()
+    v, ms = capi.wp_wprod_tune(Ad, Bd, L, prec="bf16x3")
+    assert v in (1, 2) and ms > 0
+    assert capi.wp_plan_get(n1, n2, n4, p, L, "bf16x3") == v
+    C = host(capi.wp_wprod(Ad, Bd, L, prec="bf16x3"))
+    assert O.rel_fro(C, O.wprod(A, B, L)) <= TOL_X3
+    # FP32 has a single kernel: nothing to tune
+    assert capi.wp_wprod_tune(Ad, Bd, L, prec="fp32") == (0, 0.0)
+    capi.wp_plan_clear()
+    assert capi.wp_get_device_error() == 0
