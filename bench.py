@@ -56,7 +56,8 @@ def parse_args():
                     help="print the oracle's timings on this host as JSON and exit (used by the cpu baseline)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
-    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "sgemm", "wprod", "wprod_fp8", "jacobi", "batched"],
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "sgemm", "wprod", "wprod_fp8", "jacobi",
+                                               "batched", "glift", "jacobi_global", "wprod_fused", "lift_inverse"],
                     default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
@@ -864,6 +865,25 @@ def run_profile_case(case):
         # 72 slices of 256 x 256: 2-CTA clusters as in the full workload, one wave
         A = torch.from_numpy(synth.hsi_cube(256, 256, 72, seed=0, dtype=np.float32)).cuda()
         capi.wp_wsvd(A, 3, 20)
+    elif case == "glift":
+        # general operators (CDF-5/3-style predict + update, Sec. II-A Eq. 2), 192 x 256 x 256, L = 3 (50 MB in)
+        ops = [((-1, (0.5, 0.5)), (0, (0.25, 0.25)))] * 3
+        x = torch.from_numpy(synth.hsi_cube(256, 256, 192, seed=0, dtype=np.float32)).cuda()
+        capi.wp_glift(x, 3, ops)
+    elif case == "jacobi_global":
+        # w-svd of 4 slices of 1476 x 256 (L = 2): beyond a cluster's shared memory
+        A = torch.from_numpy(synth.hsi_cube(1476, 256, 4, seed=0, dtype=np.float32)).cuda()
+        capi.wp_wsvd(A, 2, 20)
+    elif case == "wprod_fused":
+        # the fused inverse-lift epilogue kernel at the benchmark's shape (forced through the plan cache)
+        A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
+        w = WORKLOAD
+        capi.wp_plan_set(w["n1"], w["n2"], w["n4"], w["p"], w["L"], "bf16x3", "fused")
+        capi.wp_wprod(A, B, w["L"], prec="bf16x3")
+    elif case == "lift_inverse":
+        # exported Mallat-order inverse at L = 4: 256 slices of 1024 x 512 (537 MB in)
+        y = torch.rand((256, 1024, 512), device="cuda")
+        capi.wp_lift_inverse(y, 4)
     elif case == "batched":
         items = synth.batch_items(count=64, seed=1)
         dev = []

@@ -10,20 +10,27 @@
 //   W^{-T}    a = even + P^T odd,  g_d = odd - U^T a,     g_s = a
 // with stencil operators (Op y)[k] = sum_t c_t y[refl(k + off + t)] under
 // half-sample symmetric extension (refl(-1 - i) = i, refl(N + i) = N - 1 - i)
-// and their exact transposes (the same taps scattered to the reflected
-// indices).  With P = I and U = I / 2 this is the lazy-Haar transform of
-// lift.cu.
+// and their exact transposes, evaluated as gathers: (Op^T y)[i] sums
+// c_t y[k] over the k with refl(k + off + t) = i, which (the stencil reaching
+// less than N) are k = i - off - t, -1 - i - off - t and 2N - 1 - i - off - t
+// whenever they lie in [0, N).  With P = I and U = I / 2 this is the
+// lazy-Haar transform of lift.cu.
 //
 // The operators couple neighbouring tube positions across the 2^L-slice
 // groups of the Haar transform, so the transform is no longer local to a
-// group: one thread owns one whole mode-3 tube (all p slices of one plane
-// element), held in shared memory as a [p][32] column of its warp's tile
-// (consecutive threads on consecutive banks), and runs every level on it.
-// Each tube element is read from HBM once and written once (loads and
-// stores coalesced across the warp's 32 plane elements).
+// group: a CTA owns 32 whole mode-3 tubes (all p slices of 32 consecutive
+// plane elements), held in shared memory as [p][32] tiles (the 32 tubes of
+// a slice on 32 consecutive banks).  Four threads share a tube -- one in
+// each of the CTA's four warps -- and split every pass of every level over
+// k, with a CTA barrier between passes.  A spatial input tile arrives by
+// p bulk copies of one 128-byte slice row each (cp.async.bulk, one
+// mbarrier, bounded wait); Mallat-ordered inputs are read level by level.
+// Each tube element is read from HBM once and written once (stores
+// coalesced across the 32 tubes).
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace wp {
 
@@ -35,7 +42,9 @@ struct GLevels {
   GOp P[WP_MAX_LEVELS], U[WP_MAX_LEVELS];
 };
 
-constexpr int kGTile = 32;           // plane elements (threads) per CTA
+constexpr int kGTile = 32;           // tubes (plane elements) per CTA
+constexpr int kGParts = 4;           // threads per tube
+constexpr int kGThreads = kGTile * kGParts;
 
 __device__ __forceinline__ int refl(int i, int n) {
   // half-sample symmetric extension; stencils reach less than n (host check)
@@ -44,100 +53,143 @@ __device__ __forceinline__ int refl(int i, int n) {
   return i;
 }
 
-// out[k] (+)= (Op y)[k], k < n; y[i] at y0[i * ys], out at o0[k * os]
+// (Op y)[k], k < n; y[i] at y0[i * ys]
 __device__ __forceinline__ float op_at(const GOp& op, const float* y0, int ys, int k, int n) {
   float acc = 0.f;
   for (int t = 0; t < op.len; ++t) acc = fmaf(op.c[t], y0[refl(k + op.off + t, n) * ys], acc);
   return acc;
 }
 
-// out[i] += sign * (Op^T y)[i] for all i < n (scatter of the taps)
-__device__ __forceinline__ void op_transpose_add(const GOp& op, const float* y0, int ys, float* o0, int os, int n,
-                                                 float sign) {
-  for (int k = 0; k < n; ++k) {
-    const float v = sign * y0[k * ys];
-    for (int t = 0; t < op.len; ++t) {
-      const int i = refl(k + op.off + t, n);
-      o0[i * os] = fmaf(op.c[t], v, o0[i * os]);
-    }
+// (Op^T y)[i], i < n: the three preimages of i under k -> refl(k + off + t)
+__device__ __forceinline__ float opT_at(const GOp& op, const float* y0, int ys, int i, int n) {
+  float acc = 0.f;
+  for (int t = 0; t < op.len; ++t) {
+    const int k0 = i - op.off - t, k1 = -1 - i - op.off - t, k2 = 2 * n - 1 - i - op.off - t;
+    if (k0 >= 0 && k0 < n) acc = fmaf(op.c[t], y0[k0 * ys], acc);
+    if (k1 >= 0 && k1 < n) acc = fmaf(op.c[t], y0[k1 * ys], acc);
+    if (k2 >= 0 && k2 < n) acc = fmaf(op.c[t], y0[k2 * ys], acc);
   }
+  return acc;
 }
 
-// OP: 0 forward, 1 inverse, 2 W^T, 3 W^{-T}.  One thread per plane element.
+__device__ __forceinline__ void bulk_row(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   ptx::smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(ptx::smem_u32(bar))
+               : "memory");
+}
+
+// OP: 0 forward, 1 inverse, 2 W^T, 3 W^{-T}.  bulk: the spatial input (OP 0,
+// 3) arrives by bulk copies (plane % 4 == 0, 16-byte aligned input).
 template <int OP>
-__global__ void __launch_bounds__(kGTile) glift_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                       int64_t plane, int p, int L, GLevels lv) {
-  extern __shared__ float sm[];      // two buffers [p][kGTile]
-  const int t = threadIdx.x;
-  const int64_t e = int64_t(blockIdx.x) * kGTile + t;
+__global__ void __launch_bounds__(kGThreads) glift_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                          int64_t plane, int p, int L, GLevels lv, int bulk,
+                                                          int* status) {
+  extern __shared__ __align__(128) float sm[];      // two buffers [p][kGTile]
+  __shared__ __align__(8) uint64_t bar;
+  constexpr int S = kGTile;                           // stride between tube positions in a buffer
+  const int t = int(threadIdx.x) % kGTile, part = int(threadIdx.x) / kGTile;
+  const int64_t e0 = int64_t(blockIdx.x) * kGTile, e = e0 + t;
   const bool act = e < plane;
   float* cur = sm + t;
   float* nxt = sm + size_t(p) * kGTile + t;
-  constexpr int S = kGTile;          // stride between tube positions in a buffer
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (OP == 0 || OP == 3) {
     // spatial tube in, coefficients out: finest level first
-    if (act)
-      for (int k = 0; k < p; ++k) cur[k * S] = __ldg(in + k * plane + e);
+    if (bulk) {
+      const int width = int(plane - e0 < kGTile ? plane - e0 : int64_t(kGTile));
+      __shared__ int s_ok;
+      if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        ptx::fence_mbar_init();
+        ptx::mbar_arrive_expect_tx(&bar, uint32_t(p) * uint32_t(width) * 4u);
+        for (int k = 0; k < p; ++k) bulk_row(sm + k * S, in + k * plane + e0, uint32_t(width) * 4u, &bar);
+        // one bounded wait for the CTA; on expiry (status word set) wait once
+        // more, bounded, for the copies still in flight, and give up
+        s_ok = ptx::mbar_wait(&bar, 0, status) ? 1 : 0;
+        if (!s_ok) ptx::mbar_wait(&bar, 0, nullptr, 100000000ull);
+      }
+      __syncthreads();
+      if (!s_ok) return;
+      ptx::mbar_try_wait(&bar, 0);   // completed phase: orders the copied data before this thread's reads
+    } else if (act) {
+      for (int k = part; k < p; k += kGParts) cur[k * S] = __ldg(in + k * plane + e);
+    }
+    __syncthreads();
     for (int j = 1; j <= L; ++j) {
       const int h = p >> j;
       const GOp& P = lv.P[j - 1];
       const GOp& U = lv.U[j - 1];
-      if (!act) continue;
       if (OP == 0) {
-        // d -> nxt[h..2h) and out; s -> nxt[0..h)
-        for (int k = 0; k < h; ++k) {
-          const float d = cur[(2 * k) * S] - op_at(P, cur + S, 2 * S, k, h);
-          nxt[(h + k) * S] = d;
-          out[int64_t(h + k) * plane + e] = d;
-        }
-        for (int k = 0; k < h; ++k) nxt[k * S] = cur[(2 * k + 1) * S] + op_at(U, nxt + h * S, S, k, h);
+        // d -> nxt[h..2h) and out, then s -> nxt[0..h)
+        if (act)
+          for (int k = part; k < h; k += kGParts) {
+            const float d = cur[(2 * k) * S] - op_at(P, cur + S, 2 * S, k, h);
+            nxt[(h + k) * S] = d;
+            out[int64_t(h + k) * plane + e] = d;
+          }
+        __syncthreads();
+        if (act)
+          for (int k = part; k < h; k += kGParts) nxt[k * S] = cur[(2 * k + 1) * S] + op_at(U, nxt + h * S, S, k, h);
       } else {
-        // a = even + P^T odd -> nxt[0..h); g_d = odd - U^T a -> nxt[h..2h) and out
-        for (int k = 0; k < h; ++k) {
-          nxt[k * S] = cur[(2 * k + 1) * S];
-          nxt[(h + k) * S] = cur[(2 * k) * S];
-        }
-        op_transpose_add(P, cur, 2 * S, nxt, S, h, 1.f);
-        op_transpose_add(U, nxt, S, nxt + h * S, S, h, -1.f);
-        for (int k = 0; k < h; ++k) out[int64_t(h + k) * plane + e] = nxt[(h + k) * S];
+        // a = even + P^T odd -> nxt[0..h), then g_d = odd - U^T a -> nxt[h..2h) and out
+        if (act)
+          for (int k = part; k < h; k += kGParts) nxt[k * S] = cur[(2 * k + 1) * S] + opT_at(P, cur, 2 * S, k, h);
+        __syncthreads();
+        if (act)
+          for (int k = part; k < h; k += kGParts) {
+            const float gd = cur[(2 * k) * S] - opT_at(U, nxt, S, k, h);
+            nxt[(h + k) * S] = gd;
+            out[int64_t(h + k) * plane + e] = gd;
+          }
       }
+      __syncthreads();
       float* tmp = cur;
       cur = nxt;
       nxt = tmp;
     }
     if (act)
-      for (int k = 0; k < (p >> L); ++k) out[k * plane + e] = cur[k * S];
+      for (int k = part; k < (p >> L); k += kGParts) out[k * plane + e] = cur[k * S];
   } else {
     // coefficients in, spatial tube out: coarsest level first
     if (act)
-      for (int k = 0; k < (p >> L); ++k) cur[k * S] = __ldg(in + k * plane + e);
+      for (int k = part; k < (p >> L); k += kGParts) cur[k * S] = __ldg(in + k * plane + e);
     for (int j = L; j >= 1; --j) {
       const int h = p >> j;
       const GOp& P = lv.P[j - 1];
       const GOp& U = lv.U[j - 1];
-      if (!act) continue;
-      for (int k = 0; k < h; ++k) nxt[(h + k) * S] = __ldg(in + int64_t(h + k) * plane + e);
+      if (act)
+        for (int k = part; k < h; k += kGParts) nxt[(h + k) * S] = __ldg(in + int64_t(h + k) * plane + e);
+      __syncthreads();
       if (OP == 1) {
-        // even = s - U(d) -> nxt[0..h); f[2k+1] = even, f[2k] = d + P(even) -> cur[0..2h)
-        for (int k = 0; k < h; ++k) nxt[k * S] = cur[k * S] - op_at(U, nxt + h * S, S, k, h);
-        for (int k = 0; k < h; ++k) {
-          cur[(2 * k + 1) * S] = nxt[k * S];
-          cur[(2 * k) * S] = nxt[(h + k) * S] + op_at(P, nxt, S, k, h);
-        }
+        // even = s - U(d) -> nxt[0..h); then f[2k+1] = even, f[2k] = d + P(even) -> cur[0..2h)
+        if (act)
+          for (int k = part; k < h; k += kGParts) nxt[k * S] = cur[k * S] - op_at(U, nxt + h * S, S, k, h);
+        __syncthreads();
+        if (act)
+          for (int k = part; k < h; k += kGParts) {
+            cur[(2 * k + 1) * S] = nxt[k * S];
+            cur[(2 * k) * S] = nxt[(h + k) * S] + op_at(P, nxt, S, k, h);
+          }
       } else {
-        // b = g_d + U^T g_s -> nxt[h..2h); g_even = g_s - P^T b -> nxt[0..h)
-        op_transpose_add(U, cur, S, nxt + h * S, S, h, 1.f);
-        for (int k = 0; k < h; ++k) nxt[k * S] = cur[k * S];
-        op_transpose_add(P, nxt + h * S, S, nxt, S, h, -1.f);
-        for (int k = 0; k < h; ++k) {
-          cur[(2 * k + 1) * S] = nxt[k * S];
-          cur[(2 * k) * S] = nxt[(h + k) * S];
-        }
+        // b = g_d + U^T g_s -> nxt[h..2h) (in place: each k reads its own g_d);
+        // g_even = g_s - P^T b -> nxt[0..h); then interleave into cur[0..2h)
+        if (act)
+          for (int k = part; k < h; k += kGParts) nxt[(h + k) * S] += opT_at(U, cur, S, k, h);
+        __syncthreads();
+        if (act)
+          for (int k = part; k < h; k += kGParts) nxt[k * S] = cur[k * S] - opT_at(P, nxt + h * S, S, k, h);
+        __syncthreads();
+        if (act)
+          for (int k = part; k < h; k += kGParts) {
+            cur[(2 * k + 1) * S] = nxt[k * S];
+            cur[(2 * k) * S] = nxt[(h + k) * S];
+          }
       }
+      __syncthreads();
     }
     if (act)
-      for (int k = 0; k < p; ++k) out[k * plane + e] = cur[k * S];
+      for (int k = part; k < p; k += kGParts) out[k * plane + e] = cur[k * S];
   }
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
@@ -178,6 +230,7 @@ template <int OP>
 static int launch_glift(const float* in, float* out, int64_t plane, int64_t p, int L, const GLevels& lv,
                         cudaStream_t st) {
   const size_t smem = size_t(2) * p * kGTile * sizeof(float);
+  const int bulk = (OP == 0 || OP == 3) && plane % 4 == 0 && aligned16(in);
   static bool attr = false;
   if (!attr) {
     WP_CUDA_TRY(cudaFuncSetAttribute(glift_kernel<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -186,7 +239,7 @@ static int launch_glift(const float* in, float* out, int64_t plane, int64_t p, i
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned((plane + kGTile - 1) / kGTile), 1, 1);
-  cfg.blockDim = dim3(kGTile, 1, 1);
+  cfg.blockDim = dim3(kGThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attrs[1];
@@ -196,7 +249,7 @@ static int launch_glift(const float* in, float* out, int64_t plane, int64_t p, i
   cfg.numAttrs = 1;
   static const char* const names[4] = {"glift_forward", "glift_inverse", "glift_adjoint", "glift_inverse_adjoint"};
   WP_PROFILE(names[OP], st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, glift_kernel<OP>, in, out, plane, int(p), L, lv));
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, glift_kernel<OP>, in, out, plane, int(p), L, lv, bulk, device_status_ptr()));
   return launch_status();
 }
 

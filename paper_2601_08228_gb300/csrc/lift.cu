@@ -85,7 +85,10 @@ __device__ __forceinline__ void store_vec(float* p, const float* v) {
 // gather a group from its Mallat positions at L >= 4, where it streams
 // faster (measured at 256 slices of 1024 x 512: 4.4 against 3.5 TB/s at
 // L = 4, 2.8 against 2.2 TB/s at L = 5).
-template <int L, int VEC, int OP, bool IL, bool GF>
+// S2: the coarse pass of a split inverse / adjoint (see launch_split): local
+// index t of group g is written to output slice 4 (g G + t) + 3 instead of
+// g G + t.
+template <int L, int VEC, int OP, bool IL, bool GF, bool S2 = false>
 __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__ in,
                                                        float* __restrict__ out, int64_t plane,
                                                        int64_t p, int64_t nvec, int64_t total) {
@@ -126,9 +129,55 @@ __global__ void __launch_bounds__(256) lift_reg_kernel(const float* __restrict__
     }
 #pragma unroll
     for (int t = 0; t < G; ++t) {
-      const int64_t slice = (reads_spatial(OP) && !IL) ? mallat_slice<L>(t, g, p) : g * G + t;
+      int64_t slice = (reads_spatial(OP) && !IL) ? mallat_slice<L>(t, g, p) : g * G + t;
+      if constexpr (S2) slice = 4 * slice + 3;
       store_vec<VEC>(out + slice * plane + e, w2[t]);
     }
+  }
+}
+
+// Fine pass of a split inverse / adjoint: the last two levels (L = 2 groups
+// of four slices k) with the smooth coefficient s_2[k] taken from slice
+// 4k + 3 of x, where the coarse pass left it; d_2 and d_1 from their Mallat
+// positions in y (p/4 + k, p/2 + 2k, p/2 + 2k + 1).  Every thread reads its
+// element of slice 4k + 3 before it writes slices 4k .. 4k + 3 of the same
+// element, so reusing x needs no synchronisation (x is not __restrict__).
+template <int VEC, int OP>
+__global__ void __launch_bounds__(256) lift_tail_kernel(const float* __restrict__ y, float* x, int64_t plane,
+                                                        int64_t p, int64_t nvec, int64_t total) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  for (int64_t w = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; w < total; w += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t k = w / nvec;
+    const int64_t e = (w - k * nvec) * VEC;
+    float v[4][VEC];
+    {
+      const float* src = x + (4 * k + 3) * plane + e;   // written by the coarse pass: read through L2
+      if constexpr (VEC == 4) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(src));
+        v[0][0] = q.x; v[0][1] = q.y; v[0][2] = q.z; v[0][3] = q.w;
+      } else if constexpr (VEC == 2) {
+        const float2 q = __ldcg(reinterpret_cast<const float2*>(src));
+        v[0][0] = q.x; v[0][1] = q.y;
+      } else {
+        v[0][0] = __ldcg(src);
+      }
+    }
+    load_vec<VEC>(y + ((p >> 2) + k) * plane + e, v[1]);
+    load_vec<VEC>(y + ((p >> 1) + 2 * k) * plane + e, v[2]);
+    load_vec<VEC>(y + ((p >> 1) + 2 * k + 1) * plane + e, v[3]);
+    float o[4][VEC];
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) {
+      float a[4], b[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) a[t] = v[t][c];
+      group_op<2, OP>(a, b);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) o[t][c] = b[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) store_vec<VEC>(x + (4 * k + t) * plane + e, o[t]);
   }
 }
 
@@ -208,7 +257,7 @@ __global__ void __launch_bounds__(256) lift_smem_kernel(const float* __restrict_
   }
 }
 
-template <int L, int VEC, int OP, bool IL>
+template <int L, int VEC, int OP, bool IL, bool S2 = false>
 static int launch_reg(const float* in, float* out, int64_t plane, int64_t p, cudaStream_t st) {
   const int64_t nvec = plane / VEC;
   const int64_t total = (p >> L) * nvec;
@@ -229,7 +278,37 @@ static int launch_reg(const float* in, float* out, int64_t plane, int64_t p, cud
   // group-fastest chunk order for the Mallat-position gathers at L >= 4
   constexpr bool GF = !IL && !reads_spatial(OP) && L >= 4;
   WP_PROFILE(kLiftNames[OP], st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP, IL, GF>, in, out, plane, p, nvec, total));
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_reg_kernel<L, VEC, OP, IL, GF, S2>, in, out, plane, p, nvec, total));
+  return launch_status();
+}
+
+// Mallat-input inverse / adjoint at L = 4, 5, split by levels.  Gathering a
+// group from its L + 1 Mallat runs reads far below the copy rate at L >= 4
+// (measured 4.4 / 2.8 TB/s at L = 4 / 5 against 5.5 at L = 3, 256 slices of
+// 1024 x 512), so the transform runs as two passes with short gathers:
+//   coarse  levels L .. 3 on the first p/4 slices of y -- the Mallat-ordered
+//           (L-2)-level transform of s_2 -- writing s_2[k] to slice 4k + 3 of x;
+//   fine    levels 2 and 1 (lift_tail_kernel), s_2 from x, d_2, d_1 from y.
+// x (the output, distinct from y) doubles as the scratch space; the extra
+// traffic is p/4 slices written and read once (2.5 p slices moved against 2 p).
+template <int L, int VEC, int OP>
+static int launch_split(const float* y, float* x, int64_t plane, int64_t p, cudaStream_t st) {
+  static_assert(L == 4 || L == 5, "split passes for L = 4, 5");
+  WP_TRY((launch_reg<L - 2, VEC, OP, false, true>(y, x, plane, p >> 2, st)));
+  const int64_t nvec = plane / VEC;
+  const int64_t total = (p >> 2) * nvec;
+  int64_t blocks = std::min<int64_t>((total + 255) / 256, int64_t(sm_count()) * 8);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(std::max<int64_t>(blocks, 1)), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  WP_PROFILE(kLiftNames[OP], st);
+  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, lift_tail_kernel<VEC, OP>, y, x, plane, p, nvec, total));
   return launch_status();
 }
 
@@ -268,6 +347,13 @@ template <int OP, bool IL>
 static int dispatch(const float* in, float* out, int64_t plane, int64_t p, int L, cudaStream_t st) {
   const bool v4 = (plane % 4 == 0) && aligned16(in) && aligned16(out);
   const bool v2 = (plane % 2 == 0);
+  // Mallat-input ops at L = 4, 5 with a separate output: two passes (launch_split)
+  if constexpr (!IL && !reads_spatial(OP)) {
+    if ((L == 4 || L == 5) && in != out) {
+      if (L == 4) return v4 ? launch_split<4, 4, OP>(in, out, plane, p, st) : launch_split<4, 1, OP>(in, out, plane, p, st);
+      return v4 ? launch_split<5, 4, OP>(in, out, plane, p, st) : launch_split<5, 1, OP>(in, out, plane, p, st);
+    }
+  }
   switch (L) {
     case 0: return v4 ? launch_reg<0, 4, OP, IL>(in, out, plane, p, st) : launch_reg<0, 1, OP, IL>(in, out, plane, p, st);
     case 1: return v4 ? launch_reg<1, 4, OP, IL>(in, out, plane, p, st) : launch_reg<1, 1, OP, IL>(in, out, plane, p, st);

@@ -178,3 +178,38 @@ def test_fp8_quant_rows_two_operands_once(p, L, plane_a, plane_b, vec, blocks):
     # the grid-stride loop itself: every item index exactly once
     visits = [it for b in range(blocks) for t in range(256) for it in range(b * 256 + t, total, blocks * 256)]
     assert sorted(visits) == list(range(total))
+
+
+@pytest.mark.parametrize("L", [4, 5])
+@pytest.mark.parametrize("op", ["inverse", "adjoint"])
+def test_split_mallat_inverse_maps(L, op):
+    """The two-pass Mallat-input inverse / adjoint at L = 4, 5 (lift.cu,
+    launch_split), restated on the CPU: the coarse pass applies the
+    (L-2)-level transform to the first p/4 coefficient slices and writes
+    s_2[k] to output slice 4k + 3; the fine pass reads s_2[k] there and d_2,
+    d_1 from their Mallat positions and writes slices 4k .. 4k + 3.  Every
+    slice index stays in bounds, every output slice is written once by the
+    fine pass, and the result equals the one-pass transform."""
+    import oracle as O
+    p = 3 << L                                    # three tube groups
+    y = np.random.default_rng(L).uniform(-1, 1, size=(p, 2, 3))
+    one = O.ilift if op == "inverse" else O.lift_adjoint
+    x = np.full_like(y, np.nan)
+    # coarse pass
+    s2 = one(y[: p // 4], L - 2)                  # natural order, p/4 slices
+    for k in range(p // 4):
+        assert 0 <= 4 * k + 3 < p
+        x[4 * k + 3] = s2[k]
+    # fine pass
+    written = np.zeros(p, dtype=int)
+    for k in range(p // 4):
+        src = [4 * k + 3, p // 4 + k, p // 2 + 2 * k, p // 2 + 2 * k + 1]
+        assert all(0 <= i < p for i in src)
+        grp = np.stack([x[src[0]], y[src[1]], y[src[2]], y[src[3]]])
+        out = one(grp, 2)
+        for t in range(4):
+            x[4 * k + t] = out[t]
+            written[4 * k + t] += 1
+    assert np.all(written == 1)
+    np.testing.assert_allclose(x, one(y, L), rtol=0, atol=1e-14)
+
