@@ -709,6 +709,30 @@ def _extras(capi, args):
     out["batched_4096"] = {"tensors_per_s": 4096 / t, "ms": t * 1e3, "graph": True,
                            "gemm_threads": bl.plan.gemm_threads, "svd_threads": bl.plan.svd_threads}
     del dev, bl, g
+    # the w-svd and sp-w-svd of the workload with the Jacobi SVD's QR preconditioning switched
+    # off (the timed steps run with it on): time and sweeps per slice of both variants
+    from paper_2601_08228_gb300 import synth as _s
+    Aw = torch.from_numpy(_s.hsi_cube(256, 256, 192, seed=0, dtype=np.float32)).cuda()
+    pre = {}
+    for on in (True, False):
+        capi.wp_set_jacobi_precondition(on)
+        for sp in (False, True):
+            for _ in range(2):
+                capi.wp_wsvd(Aw, 3, 20, sparse=sp)
+            torch.cuda.synchronize()
+            capi.wp_jacobi_stats()
+            a.record()
+            for _ in range(5):
+                capi.wp_wsvd(Aw, 3, 20, sparse=sp)
+            b.record()
+            torch.cuda.synchronize()
+            tot, mx = capi.wp_jacobi_stats()
+            nsl = 48 if sp else 192
+            pre[f"{'spwsvd' if sp else 'wsvd'}_{'qr' if on else 'plain'}"] = {
+                "ms": a.elapsed_time(b) / 5, "sweeps_per_slice": tot / (5 * nsl), "max_sweeps": mx}
+    capi.wp_set_jacobi_precondition(True)
+    out["jacobi_qr_preconditioning"] = pre
+    del Aw
     # deblurring step at 512 x 512 x 128, L = 4
     n, p, L = 512, 128, 4
     K = synth.blur_operator(n, p, dtype=np.float32)

@@ -128,6 +128,22 @@ WP_API int wp_jacobi_stats(int64_t* total_sweeps, int* max_sweeps);
  * calls in flight on other host threads. */
 WP_API int wp_set_jacobi_max_sweeps(int max_sweeps);
 
+/* QR preconditioning of the facewise Jacobi SVD of wp_wsvd (on = 1, the
+ * default; 0 = off; else WP_ERR_SHAPE).  wp_wpinv and wp_deblur_pinv always
+ * use the plain Jacobi: a pseudo-inverse needs every singular value down to
+ * its cut-off (max(m, n) eps sigma_max), and at that level the columns of
+ * R^T fall below the Jacobi's numerically-zero threshold.  For
+ * slices with 32 <= min(n1, n2) and max(n1, n2) <= 1024 the working matrix X
+ * (the slice, or its transpose when it is wide) is first factored X = Q R by
+ * Householder reflections, and the one-sided Jacobi method runs on the
+ * columns of R^T, which converges in fewer sweeps; its converged columns
+ * give the singular values and the singular vectors of X's short side,
+ * from which the rank-r reconstruction, the factors and the pseudo-inverse
+ * follow as before (Q is never formed).  Same results within the stated
+ * tolerances; the workspace queries include the QR's work buffer.
+ * Process-wide; applies to calls made after it (query workspaces after it). */
+WP_API int wp_set_jacobi_precondition(int on);
+
 /* Synchronise `stream`, then return and clear the device status word of the
  * current device (WP_OK if no kernel reported a fault since the last call).
  * Returns WP_ERR_CUDA if the synchronisation itself fails. */

@@ -69,6 +69,7 @@ _SIGNATURES = {
     "wp_get_device_error": ([_P], _I),
     "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
     "wp_set_jacobi_max_sweeps": ([_I], _I),
+    "wp_set_jacobi_precondition": ([_I], _I),
     "wp_selftest_bounded_wait": ([_I, _I64, _P], _I),
     "wp_wprod_tune": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P, ctypes.POINTER(_I),
                        ctypes.POINTER(ctypes.c_double)], _I),
@@ -547,6 +548,11 @@ def wp_jacobi_stats():
 def wp_set_jacobi_max_sweeps(n):
     """Set the Jacobi sweep limit of later launches (default 40)."""
     _check(lib().wp_set_jacobi_max_sweeps(int(n)), "wp_set_jacobi_max_sweeps")
+
+
+def wp_set_jacobi_precondition(on):
+    """QR preconditioning of the Jacobi SVD on (True, default) or off."""
+    _check(lib().wp_set_jacobi_precondition(int(bool(on))), "wp_set_jacobi_precondition")
 
 
 def wp_selftest_bounded_wait(which, limit_ns):

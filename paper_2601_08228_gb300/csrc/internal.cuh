@@ -57,6 +57,16 @@ size_t jacobi_global_work_bytes(int n1, int n2, int nslices);
 bool jacobi_global_supported(int n1, int n2);
 struct JacobiArgs;
 int jacobi_global_launch(const JacobiArgs& a, int nslices, void* work, size_t work_bytes, cudaStream_t st);
+// Householder QR preconditioner of the Jacobi SVD (qr.cu): R^T (row-major)
+// of the working matrix of each of slices [0, nslices) of X (p, n1, n2).
+bool qr_supported(int m_len, int n_vec);
+size_t qr_work_bytes(int m_len, int n_vec, int nslices);
+int qr_r(const float* X, int n1, int n2, int nslices, void* work, size_t work_bytes, float** Rt_out,
+         cudaStream_t st);
+// True when w-svd / wpinv precondition the Jacobi SVD of (n1, n2) slices by
+// a QR (setting of wp_set_jacobi_precondition, and the slice shape: at
+// least 32 columns, at most 1024 rows, within the register kernel's reach).
+bool jacobi_preconditioned(int n1, int n2);
 // Device address of the Jacobi sweep counters ([0] total slice-sweeps, [1] max).
 unsigned long long* jacobi_stats_ptr();
 // Sweep limit passed to every Jacobi launch (default kJacobiMaxSweeps; set by

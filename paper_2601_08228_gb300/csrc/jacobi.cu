@@ -403,11 +403,25 @@ size_t jacobi_work_bytes(int n1, int n2, int nslices) {
   return cluster_fits(n1, n2) ? 0 : jacobi_global_work_bytes(n1, n2, nslices);
 }
 
+static std::atomic<int> g_jacobi_precondition{1};
+
+bool jacobi_preconditioned(int n1, int n2) {
+  const int m_len = std::max(n1, n2), n_vec = std::min(n1, n2);
+  return g_jacobi_precondition.load(std::memory_order_relaxed) != 0 && n_vec >= 32 && qr_supported(m_len, n_vec) &&
+         cluster_fits(n_vec, n_vec);
+}
+
 }  // namespace wp
 
 extern "C" int wp_set_jacobi_max_sweeps(int max_sweeps) {
   if (max_sweeps < 1 || max_sweeps > 1000) return WP_ERR_SHAPE;
   wp::g_jacobi_max_sweeps.store(max_sweeps, std::memory_order_relaxed);
+  return WP_OK;
+}
+
+extern "C" int wp_set_jacobi_precondition(int on) {
+  if (on != 0 && on != 1) return WP_ERR_SHAPE;
+  wp::g_jacobi_precondition.store(on, std::memory_order_relaxed);
   return WP_OK;
 }
 

@@ -148,6 +148,33 @@ static unsigned grid_for(int64_t total) {
 
 // ---- w-svd ------------------------------------------------------------------------
 
+// Work of the QR preconditioner (0 when the shape is not preconditioned).
+static size_t precond_bytes(int64_t n1, int64_t n2, int64_t p) {
+  if (!jacobi_preconditioned(int(n1), int(n2))) return 0;
+  return qr_work_bytes(int(std::max(n1, n2)), int(std::min(n1, n2)), int(p));
+}
+
+// Facewise Jacobi SVD of slices [0, nsl) of Ah, preconditioned by a QR where
+// jacobi_preconditioned() says so.  *right = true when the vectors written
+// to vec are right singular vectors (n2 x r per slice), false for left ones
+// (n1 x r): the plain Jacobi yields the long side's vectors, the
+// preconditioned one (Jacobi on R^T) the short side's.
+static int facewise_svd(const float* Ah, int64_t n1, int64_t n2, int nsl, int r, float* vec, float* sig, void* qwork,
+                        size_t qbytes, void* jwork, size_t jbytes, bool* right, cudaStream_t st) {
+  const int N1 = int(n1), N2 = int(n2);
+  if (qbytes > 0) {
+    float* Rt = nullptr;
+    WP_TRY(qr_r(Ah, N1, N2, nsl, qwork, qbytes, &Rt, st));
+    const int nv = std::min(N1, N2);
+    WP_TRY(jacobi_svd(Rt, nv, nv, 0, nsl, r, vec, sig, st));
+    *right = n1 >= n2;
+    return WP_OK;
+  }
+  WP_TRY(jacobi_svd(Ah, N1, N2, 0, nsl, r, vec, sig, st, jwork, jbytes));
+  *right = n1 < n2;
+  return WP_OK;
+}
+
 static void wsvd_layout(int64_t n1, int64_t n2, int64_t p, int r, Sizer& s) {
   const int64_t mx = std::max(n1, n2);
   s.take<float>(size_t(p) * n1 * n2);   // A_hat
@@ -159,6 +186,7 @@ static void wsvd_layout(int64_t n1, int64_t n2, int64_t p, int r, Sizer& s) {
   s.take<float>(size_t(p) * r);         //                              S
   s.take<float>(size_t(p) * n2 * r);    //                              V
   s.take<char>(jacobi_work_bytes(int(n1), int(n2), int(p)));   // large slices: Jacobi work buffer
+  s.take<char>(precond_bytes(n1, n2, p));                        // QR preconditioner
 }
 
 static int check_wsvd(int64_t n1, int64_t n2, int64_t p, int L, int r) {
@@ -212,15 +240,17 @@ extern "C" int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V,
   float* Vw = cv.take<float>(size_t(p) * n2 * r);
   const size_t jw = jacobi_work_bytes(int(n1), int(n2), int(p));
   void* jwork = jw ? cv.take<char>(jw) : nullptr;
+  const size_t qb = precond_bytes(n1, n2, p);
+  void* qwork = qb ? cv.take<char>(qb) : nullptr;
   if (!cv.ok) return WP_ERR_WORKSPACE;
   cudaStream_t st = as_stream(stream);
   const int N1 = int(n1), N2 = int(n2);
   const int64_t m = p >> L;
   const int nsl = int(sparse ? std::min<int64_t>(2 * m, p) : p);
-  const bool trans = n1 < n2;
 
   WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, n1 * n2, p, L, st));
-  WP_TRY(jacobi_svd(Ah, N1, N2, 0, nsl, r, vec, sig, st, jwork, jw));
+  bool trans = false;   // the Jacobi vectors are right singular vectors
+  WP_TRY(facewise_svd(Ah, n1, n2, nsl, r, vec, sig, qwork, qb, jwork, jw, &trans, st));
   if (!trans) {
     // T = U_r^T A_hat (r x n2), C_hat = U_r T
     WP_TRY(sgemm_batched(vec, Ah, T, r, N2, N1, true, false, nsl, st));
@@ -309,25 +339,29 @@ extern "C" int wp_wpinv(const float* A, float* X, int64_t m, int64_t n, int64_t 
   const float tol = rtol < 0 ? float(mx) * 1.1920929e-7f : float(rtol);
 
   WP_TRY(lift_dispatch(LIFT_FWD, A, Ah, m * n, p, L, st));
-  WP_TRY(jacobi_svd(Ah, M, N, 0, P, K, vec, sig, st, jwork, jw));
-  if (m >= n) {
-    // U = vec (m x n); T = A^T U (n x n); T *= w; X_hat = T U^T (n x m)
-    WP_TRY(sgemm_batched(Ah, vec, T, N, N, M, true, false, P, st));
+  // the plain Jacobi: the pseudo-inverse needs every singular value down to
+  // the cut-off, and R^T's columns (R's rows, graded like the singular
+  // values) fall below the Jacobi's numerically-zero threshold there
+  bool right = false;
+  WP_TRY(facewise_svd(Ah, m, n, P, K, vec, sig, nullptr, 0, jwork, jw, &right, st));
+  if (!right) {
+    // U = vec (m x K); T = A^T U (n x K); T *= w; X_hat = T U^T (n x m)
+    WP_TRY(sgemm_batched(Ah, vec, T, N, K, M, true, false, P, st));
     {
       WP_PROFILE("pinv_scale", st);
-      pinv_scale_kernel<<<grid_for(p * n * n), 256, 0, st>>>(T, sig, N, N, P, tol);
+      pinv_scale_kernel<<<grid_for(p * n * K), 256, 0, st>>>(T, sig, N, K, P, tol);
       WP_TRY(launch_status());
     }
-    WP_TRY(sgemm_batched(T, vec, Xh, N, M, N, false, true, P, st));
+    WP_TRY(sgemm_batched(T, vec, Xh, N, M, K, false, true, P, st));
   } else {
-    // V = vec (n x m); T = A V (m x m); T *= w; X_hat = V T^T (n x m)
-    WP_TRY(sgemm_batched(Ah, vec, T, M, M, N, false, false, P, st));
+    // V = vec (n x K); T = A V (m x K); T *= w; X_hat = V T^T (n x m)
+    WP_TRY(sgemm_batched(Ah, vec, T, M, K, N, false, false, P, st));
     {
       WP_PROFILE("pinv_scale", st);
-      pinv_scale_kernel<<<grid_for(p * m * m), 256, 0, st>>>(T, sig, M, M, P, tol);
+      pinv_scale_kernel<<<grid_for(p * m * K), 256, 0, st>>>(T, sig, M, K, P, tol);
       WP_TRY(launch_status());
     }
-    WP_TRY(sgemm_batched(vec, T, Xh, N, M, M, false, true, P, st));
+    WP_TRY(sgemm_batched(vec, T, Xh, N, M, K, false, true, P, st));
   }
   for (int it = 0; it < refine_iters; ++it) {
     {

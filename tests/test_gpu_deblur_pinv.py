@@ -52,3 +52,37 @@ def test_deblur_pinv_recovers_with_invertible_operators():
     B = O.wprod(O.wprod(AV, X0, L), O.transpose(AH), L)
     X = capi.wp_deblur_pinv(dev(AV), dev(AH), dev(B), L, refine_iters=1).cpu().numpy()
     assert O.rel_fro(X, X0) <= 1e-5
+
+
+@pytest.mark.parametrize("n1,n2", [(217, 128), (128, 217)])
+def test_deblur_pinv_wide_blur_singular_detail_slices(n1, n2):
+    """The benchmark's blur width (b = 10) on a 217-pixel side: the spatial
+    operator has condition number ~2e4 and its detail slices are singular, so
+    the cut-off decides which singular values are kept.  Every singular value
+    down to the cut-off must be resolved; a Jacobi that leaves small columns
+    unrotated fails this by orders of magnitude."""
+    p, L, b = 8, 2, 10
+    AV = synth.linear_blur_operator(n1, p, b=b, dtype=np.float32)
+    AH = synth.linear_blur_operator(n2, p, b=b, dtype=np.float32)
+    B = synth.hsi_cube(n1, n2, p, rank=4, seed=11, dtype=np.float32)
+    X = capi.wp_deblur_pinv(dev(AV), dev(AH), dev(B), L, refine_iters=2).cpu().numpy()
+    ref = O.deblur_pinv(AV, AH, B, L, rtol=max(n1, n2) * EPS32)
+    kap = np.linalg.cond(AV[0].astype(np.float64)) + np.linalg.cond(AH[0].astype(np.float64))
+    err = O.rel_fro(X, ref)
+    print(f"deblur_pinv {p}x{n1}x{n2} L={L} b={b}: {err:.2e} (kappa sum {kap:.1e})")
+    assert err <= 8 * kap * EPS32, err
+    assert capi.wp_get_device_error() == 0
+
+
+def test_wpinv_wide_blur_operator():
+    """wp_wpinv alone on the b = 10 blur of a 217-pixel side (cut-off
+    217 eps32 relative), against the oracle on the same FP32 input."""
+    p, n, L, b = 8, 217, 2, 10
+    A = synth.linear_blur_operator(n, p, b=b, dtype=np.float32)
+    X = capi.wp_wpinv(dev(A), L, rtol=n * EPS32, refine_iters=2).cpu().numpy()
+    ref = O.wpinv(A, L, rtol=n * EPS32)
+    kap = np.linalg.cond(A[0].astype(np.float64))
+    err = O.rel_fro(X, ref)
+    print(f"wpinv {p}x{n}x{n} L={L} b={b}: {err:.2e} (kappa {kap:.1e})")
+    assert err <= 8 * kap * EPS32, err
+    assert capi.wp_get_device_error() == 0

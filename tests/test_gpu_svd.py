@@ -162,7 +162,8 @@ def test_wpinv_remark_2_2():
     np.testing.assert_allclose(O.wprod(Bd, Ad, 1), rem["D"], atol=0.005)
 
 
-PINV_CASES = [(8, 12, 7, 3), (8, 7, 12, 3), (24, 30, 22, 3), (24, 30, 30, 3), (16, 64, 40, 4), (4, 1, 6, 2)]
+PINV_CASES = [(8, 12, 7, 3), (8, 7, 12, 3), (24, 30, 22, 3), (24, 30, 30, 3), (16, 64, 40, 4), (4, 1, 6, 2),
+              (8, 40, 72, 3), (8, 48, 48, 3)]   # the last two: wide and square slices of 32+ columns
 
 
 def _kappa(A, L):
@@ -300,4 +301,32 @@ def test_wpinv_zero_detail_slices_large():
     A = np.broadcast_to(T, (p, n, n)).copy()
     X = host(capi.wp_wpinv(dev(A), L, refine_iters=1))
     assert O.rel_fro(X, O.wpinv(A, L)) <= 1e-4
+    assert capi.wp_get_device_error() == 0
+
+
+@pytest.mark.parametrize("n1,n2", [(96, 96), (120, 64), (64, 120)])
+def test_qr_preconditioning_fewer_sweeps_same_result(n1, n2):
+    """The QR-preconditioned Jacobi (on the columns of R^T) needs fewer
+    sweeps than the Jacobi on the slices themselves and gives the same
+    singular values and rank-r reconstruction, within the SVD bars, against
+    the oracle."""
+    p, L, r = 48, 3, 10
+    A = synth.hsi_cube(n1, n2, p, seed=3, dtype=np.float32)
+    Ad = dev(A)
+    res = {}
+    try:
+        for pre in (False, True):
+            capi.wp_set_jacobi_precondition(pre)
+            capi.wp_jacobi_stats()
+            C, _, S, _ = capi.wp_wsvd(Ad, L, r, factors=True)
+            torch.cuda.synchronize()
+            res[pre] = (host(C), host(S), capi.wp_jacobi_stats()[0])
+    finally:
+        capi.wp_set_jacobi_precondition(True)
+    Cr, _, Sr, _ = O.wsvd(A, L, r, return_factors=True)
+    tol = _rec_tol(A.astype(np.float64), L, r, p)
+    for pre in (False, True):
+        assert O.rel_fro(res[pre][1], Sr) <= TOL_SIG
+        assert O.rel_fro(res[pre][0], Cr) <= tol
+    assert res[True][2] < res[False][2]
     assert capi.wp_get_device_error() == 0

@@ -213,3 +213,64 @@ def test_split_mallat_inverse_maps(L, op):
     assert np.all(written == 1)
     np.testing.assert_allclose(x, one(y, L), rtol=0, atol=1e-14)
 
+
+
+def _blocked_qr_r(X, B=16):
+    """The steps of qr_r_kernel (qr.cu) in NumPy: panels of B columns,
+    Householder reflections H = I - tau v v^T with v[c] = 1 and
+    beta = -sign(alpha)|x|, the compact-WY T (T[c][c] = tau_c,
+    T[0:c, c] = -tau_c T[0:c, 0:c] V^T v_c), the trailing update
+    C -= V T^T V^T C; returns R^T as the kernel stores it."""
+    m, n = X.shape
+    W = X.astype(np.float64).copy()
+    Rt = np.zeros((n, n))
+    for k0 in range(0, n, B):
+        kb = min(B, n - k0)
+        V = W[k0:, k0:k0 + kb].copy()            # panel, rows relative to k0
+        tau = np.zeros(kb)
+        beta = np.zeros(kb)
+        for c in range(kb):
+            x = V[:, c]
+            alpha, s2 = x[c], float(np.sum(x[c + 1:] ** 2))
+            t, b = 0.0, alpha
+            if s2 > 0:
+                nrm = np.sqrt(alpha * alpha + s2)
+                b = -nrm if alpha >= 0 else nrm
+                t = (b - alpha) / b
+                x[c + 1:] /= (alpha - b)
+            tau[c], beta[c] = t, b
+            x[c] = 1.0
+            for j in range(c + 1, kb):
+                w = float(x[c:] @ V[c:, j]) * t
+                V[c:, j] -= w * x[c:]
+        for c in range(kb):
+            for j in range(c, kb):
+                Rt[k0 + j, k0 + c] = beta[c] if c == j else V[c, j]
+        for j in range(kb):
+            V[:j, j] = 0.0
+        T = np.zeros((kb, kb))
+        T[0, 0] = tau[0]
+        for c in range(1, kb):
+            z = V[:, :c].T @ V[:, c]
+            T[:c, c] = -tau[c] * (T[:c, :c] @ z)
+            T[c, c] = tau[c]
+        C = W[k0:, k0 + kb:]
+        C -= V @ (T.T @ (V.T @ C))
+        Rt[k0 + kb:, k0:k0 + kb] = C[:kb].T      # rows k0..k0+kb of R, trailing columns
+    return Rt
+
+
+@pytest.mark.parametrize("m,n", [(40, 33), (64, 64), (256, 48), (100, 17), (35, 35)])
+def test_blocked_qr_restatement(m, n):
+    X = np.random.default_rng(m + n).standard_normal((m, n))
+    X[:, 5] = 0.0                                  # a zero column: no reflection (tau = 0)
+    Rt = _blocked_qr_r(X)
+    R = Rt.T
+    assert np.allclose(np.tril(R, -1), 0.0)
+    Rref = np.linalg.qr(X, mode="r")
+    # R is unique up to the signs of its rows
+    sgn = np.sign(np.diag(R)) * np.sign(np.diag(Rref))
+    sgn[sgn == 0] = 1.0
+    np.testing.assert_allclose(R * sgn[:, None], Rref, atol=1e-10 * np.abs(Rref).max())
+    np.testing.assert_allclose(np.linalg.svd(R, compute_uv=False), np.linalg.svd(X, compute_uv=False), rtol=1e-10,
+                               atol=1e-12)
