@@ -56,7 +56,7 @@ def parse_args():
                     help="print the oracle's timings on this host as JSON and exit (used by the cpu baseline)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
-    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "sgemm", "wprod", "wprod_fp8", "jacobi",
+    ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "sgemm", "wprod", "wprod_fp8", "jacobi", "jacobi_row_split",
                                                "batched", "glift", "jacobi_global", "wprod_fused", "lift_inverse"],
                     default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
@@ -732,6 +732,27 @@ def _extras(capi, args):
                 "ms": a.elapsed_time(b) / 5, "sweeps_per_slice": tot / (5 * nsl), "max_sweeps": mx}
     capi.wp_set_jacobi_precondition(True)
     out["jacobi_qr_preconditioning"] = pre
+    # the same calls (QR on) with the row-split block kernel instead of the
+    # column-split one
+    ker = {}
+    for split in (True, False):
+        capi.wp_set_jacobi_column_split(split)
+        for sp in (False, True):
+            for _ in range(2):
+                capi.wp_wsvd(Aw, 3, 20, sparse=sp)
+            torch.cuda.synchronize()
+            capi.wp_jacobi_stats()
+            a.record()
+            for _ in range(5):
+                capi.wp_wsvd(Aw, 3, 20, sparse=sp)
+            b.record()
+            torch.cuda.synchronize()
+            tot, mx = capi.wp_jacobi_stats()
+            nsl = 48 if sp else 192
+            ker[f"{'spwsvd' if sp else 'wsvd'}_{'column_split' if split else 'row_split'}"] = {
+                "ms": a.elapsed_time(b) / 5, "sweeps_per_slice": tot / (5 * nsl), "max_sweeps": mx}
+    capi.wp_set_jacobi_column_split(True)
+    out["jacobi_kernels"] = ker
     del Aw
     # deblurring step at 512 x 512 x 128, L = 4
     n, p, L = 512, 128, 4
@@ -885,9 +906,11 @@ def run_profile_case(case):
         # the precision study's slice shapes at 64 slices (A 268 MB, B 134 MB), L = 4
         A, B = synth.scaled_pair(1024, 1024, 512, 64, seed=0)
         capi.wp_wprod(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 4, prec="fp8")
-    elif case == "jacobi":
-        # 72 slices of 256 x 256: 2-CTA clusters as in the full workload, one wave
+    elif case in ("jacobi", "jacobi_row_split"):
+        # 72 slices of 256 x 256: 2-CTA clusters as in the full workload, one wave;
+        # jacobi_row_split: the same call on the row-split block kernel
         A = torch.from_numpy(synth.hsi_cube(256, 256, 72, seed=0, dtype=np.float32)).cuda()
+        capi.wp_set_jacobi_column_split(case == "jacobi")
         capi.wp_wsvd(A, 3, 20)
     elif case == "glift":
         # general operators (CDF-5/3-style predict + update, Sec. II-A Eq. 2), 192 x 256 x 256, L = 3 (50 MB in)

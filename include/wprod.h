@@ -144,6 +144,15 @@ WP_API int wp_set_jacobi_max_sweeps(int max_sweeps);
  * Process-wide; applies to calls made after it (query workspaces after it). */
 WP_API int wp_set_jacobi_precondition(int on);
 
+/* Kernel choice for facewise Jacobi SVDs whose working matrix (the longer
+ * side as rows) has at most 256 rows and 192..256 columns and that would run
+ * on 2-CTA clusters: on = 1 (the default) takes the column-split kernel
+ * (each CTA holds whole columns), 0 the row-split block kernel (each CTA
+ * holds half of every column).  Both compute the same one-sided Jacobi SVD
+ * (same rotation, thresholds and stopping rule; a different pair order, so
+ * results agree to rounding).  0 or 1, else WP_ERR_SHAPE.  Process-wide. */
+WP_API int wp_set_jacobi_column_split(int on);
+
 /* Synchronise `stream`, then return and clear the device status word of the
  * current device (WP_OK if no kernel reported a fault since the last call).
  * Returns WP_ERR_CUDA if the synchronisation itself fails. */

@@ -70,6 +70,7 @@ _SIGNATURES = {
     "wp_jacobi_stats": ([ctypes.POINTER(_I64), ctypes.POINTER(_I)], _I),
     "wp_set_jacobi_max_sweeps": ([_I], _I),
     "wp_set_jacobi_precondition": ([_I], _I),
+    "wp_set_jacobi_column_split": ([_I], _I),
     "wp_selftest_bounded_wait": ([_I, _I64, _P], _I),
     "wp_wprod_tune": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P, ctypes.POINTER(_I),
                        ctypes.POINTER(ctypes.c_double)], _I),
@@ -553,6 +554,12 @@ def wp_set_jacobi_max_sweeps(n):
 def wp_set_jacobi_precondition(on):
     """QR preconditioning of the Jacobi SVD on (True, default) or off."""
     _check(lib().wp_set_jacobi_precondition(int(bool(on))), "wp_set_jacobi_precondition")
+
+
+def wp_set_jacobi_column_split(on):
+    """Column-split Jacobi kernel for the shapes it takes on (True, default) or
+    off (row-split block kernel)."""
+    _check(lib().wp_set_jacobi_column_split(int(bool(on))), "wp_set_jacobi_column_split")
 
 
 def wp_selftest_bounded_wait(which, limit_ns):

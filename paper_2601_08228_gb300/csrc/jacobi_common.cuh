@@ -87,4 +87,10 @@ __device__ __forceinline__ float multi_reduce(float (&v)[PPW], int lane) {
 // the shared-memory kernel).
 int jacobi_block_launch(const JacobiArgs& a, int nslices, cudaStream_t st);
 
+// Column-split register-resident kernel on 2-CTA clusters (jacobi_cols.cu):
+// working matrices of at most 256 rows and 192..256 columns.
+bool jacobi_cols_fits(int m_len, int n_vec);
+bool jacobi_cols_enabled();
+int jacobi_cols_launch(const JacobiArgs& a, int nslices, cudaStream_t st);
+
 }  // namespace wp

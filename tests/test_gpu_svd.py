@@ -330,3 +330,38 @@ def test_qr_preconditioning_fewer_sweeps_same_result(n1, n2):
         assert O.rel_fro(res[pre][0], Cr) <= tol
     assert res[True][2] < res[False][2]
     assert capi.wp_get_device_error() == 0
+
+
+@pytest.mark.parametrize("n1,n2,pre", [(256, 256, True), (256, 250, True), (256, 200, False), (200, 256, False)])
+def test_jacobi_column_split_matches_row_split(n1, n2, pre):
+    """The column-split kernel (whole columns per CTA, 8 rows per lane) and
+    the row-split block kernel compute the same one-sided Jacobi SVD in a
+    different pair order: both meet the SVD bars against the oracle, on the
+    QR path (R^T of 256 and of 250 columns, the latter padded to 256) and on
+    tall and wide slices without it (200 columns padded to 208; the wide one
+    works on the transpose).  48 slices: 2-CTA clusters."""
+    p, L, r = 48, 3, 20
+    A = synth.hsi_cube(n1, n2, p, seed=4, dtype=np.float32)
+    Ad = dev(A)
+    res = {}
+    try:
+        capi.wp_set_jacobi_precondition(pre)
+        for split in (False, True):
+            capi.wp_set_jacobi_column_split(split)
+            capi.wp_jacobi_stats()
+            C, _, S, _ = capi.wp_wsvd(Ad, L, r, factors=True)
+            torch.cuda.synchronize()
+            res[split] = (host(C), host(S), capi.wp_jacobi_stats())
+            assert capi.wp_get_device_error() == 0
+    finally:
+        capi.wp_set_jacobi_precondition(True)
+        capi.wp_set_jacobi_column_split(True)
+    Cr, _, Sr, _ = O.wsvd(A, L, r, return_factors=True)
+    tol = _rec_tol(A.astype(np.float64), L, r, p)
+    for split in (False, True):
+        print(f"{n1}x{n2} pre={pre} split={split}: sig {O.rel_fro(res[split][1], Sr):.2e} "
+              f"C_r {O.rel_fro(res[split][0], Cr):.2e} sweeps {res[split][2]}")
+        assert O.rel_fro(res[split][1], Sr) <= TOL_SIG
+        assert O.rel_fro(res[split][0], Cr) <= tol
+    # same method: sweep counts within one per slice of each other
+    assert abs(res[True][2][0] - res[False][2][0]) <= p
