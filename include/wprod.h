@@ -153,6 +153,24 @@ WP_API int wp_set_jacobi_precondition(int on);
  * results agree to rounding).  0 or 1, else WP_ERR_SHAPE.  Process-wide. */
 WP_API int wp_set_jacobi_column_split(int on);
 
+/* Cluster size of the column-split Jacobi kernel: 0 (the default) picks it
+ * per call -- one wave of 4- or 3-CTA clusters when every slice fits in it;
+ * else a wave of 3-CTA clusters with the few slices beyond it on 2-CTA
+ * clusters in the SMs it leaves; else full waves of 2-CTA clusters with the
+ * remaining slices beside them on 3-CTA clusters when they fit one wave of
+ * those.  Two such parts run side by side: the second on a library-owned
+ * stream of the device, forked from and joined back to the call's stream
+ * with events (both are captured when the call's stream is).  2, 3 or 4
+ * puts every launch on clusters of that size, on the call's stream.  Else
+ * WP_ERR_SHAPE.  Process-wide. */
+WP_API int wp_set_jacobi_cluster_size(int cl);
+
+/* Number of clusters of `cl` CTAs (2, 3 or 4, else WP_ERR_SHAPE) of the
+ * column-split Jacobi kernel that can be resident at once on the current
+ * device, into *clusters (0 if the occupancy query fails); WP_ERR_NULL if
+ * clusters is null. */
+WP_API int wp_jacobi_cluster_capacity(int cl, int* clusters);
+
 /* Synchronise `stream`, then return and clear the device status word of the
  * current device (WP_OK if no kernel reported a fault since the last call).
  * Returns WP_ERR_CUDA if the synchronisation itself fails. */

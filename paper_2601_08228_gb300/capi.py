@@ -71,6 +71,8 @@ _SIGNATURES = {
     "wp_set_jacobi_max_sweeps": ([_I], _I),
     "wp_set_jacobi_precondition": ([_I], _I),
     "wp_set_jacobi_column_split": ([_I], _I),
+    "wp_set_jacobi_cluster_size": ([_I], _I),
+    "wp_jacobi_cluster_capacity": ([_I, ctypes.POINTER(_I)], _I),
     "wp_selftest_bounded_wait": ([_I, _I64, _P], _I),
     "wp_wprod_tune": ([_P, _P, _P, _I64, _I64, _I64, _I64, _I, _I, _P, _SZ, _P, ctypes.POINTER(_I),
                        ctypes.POINTER(ctypes.c_double)], _I),
@@ -560,6 +562,18 @@ def wp_set_jacobi_column_split(on):
     """Column-split Jacobi kernel for the shapes it takes on (True, default) or
     off (row-split block kernel)."""
     _check(lib().wp_set_jacobi_column_split(int(bool(on))), "wp_set_jacobi_column_split")
+
+
+def wp_set_jacobi_cluster_size(cl):
+    """Cluster size of the column-split Jacobi kernel: 0 automatic, 2, 3 or 4."""
+    _check(lib().wp_set_jacobi_cluster_size(int(cl)), "wp_set_jacobi_cluster_size")
+
+
+def wp_jacobi_cluster_capacity(cl):
+    """Resident clusters of `cl` CTAs of the column-split Jacobi kernel."""
+    n = _I(0)
+    _check(lib().wp_jacobi_cluster_capacity(int(cl), ctypes.byref(n)), "wp_jacobi_cluster_capacity")
+    return int(n.value)
 
 
 def wp_selftest_bounded_wait(which, limit_ns):

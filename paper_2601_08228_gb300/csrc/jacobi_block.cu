@@ -50,11 +50,11 @@ int jacobi_block_launch(const JacobiArgs& a0, int nslices, cudaStream_t st) {
   int CL = 1;
   while (CL <= 8 && (a0.m_len + CL - 1) / CL > 32 * rpl_max) CL *= 2;
   if (CL > 8) return WP_ERR_UNSUPPORTED;
-  while (CL < 8 && 2 * CL * nslices <= sm_count()) CL *= 2;
-  // 2-CTA clusters on shapes the column-split kernel takes: use it (no
-  // per-round cluster exchange)
+  // shapes the column-split kernel takes (no per-round cluster exchange):
+  // it picks its own cluster sizes
   if (CL == 2 && jacobi_cols_enabled() && jacobi_cols_fits(a0.m_len, a0.n_vec))
     return jacobi_cols_launch(a0, nslices, st);
+  while (CL < 8 && 2 * CL * nslices <= sm_count()) CL *= 2;
   JacobiArgs a = a0;
   a.n_pad = (a0.n_pad + 2 * ppw - 1) / (2 * ppw) * (2 * ppw);
   a.rpc = (a.m_len + CL - 1) / CL;

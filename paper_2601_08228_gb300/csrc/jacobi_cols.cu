@@ -2,33 +2,37 @@
 // frontal slices (Algorithm 2: the facewise "svd" of every A_{d_j}[:, :, k]
 // and A_{s_L}[:, :, k]) for working matrices of at most 256 rows and 192..256
 // columns (the 256 x 256 slices of the benchmark cube, and the R^T factors of
-// the QR-preconditioned path).  Same rotation formula, thresholds, stopping
+// the QR-preconditioned path), on clusters of CL = 2, 3 or 4 CTAs.  Same rotation formula, thresholds, stopping
 // rule, outputs and error reporting as the block-cyclic kernel
 // (jacobi_block.cuh); only the distribution of the slice differs.
 //
-// Distribution.  A 2-CTA cluster holds one slice.  The block-cyclic kernel
-// splits the ROWS over the two CTAs, so every column pair's dot product is
-// a sum of two partials that cross the cluster every round.  Here the
-// COLUMNS are split: each CTA holds n_pad / 2 whole columns, 8 rows per lane
-// (RPL = 8, 256 rows), in blocks of PPW = 4 columns; warp w holds a "top" and
-// a "bottom" block.  A round's 4 dot products per warp are then complete
+// Distribution.  A cluster holds one slice.  The block-cyclic kernel splits
+// the ROWS over the CTAs, so every column pair's dot product is a sum of
+// partials that cross the cluster every round.  Here the COLUMNS are split:
+// each CTA holds about n_pad / CL whole columns, 8 rows per lane (RPL = 8,
+// 256 rows), in blocks of PPW = 4 columns; warp w holds a "top" and a
+// "bottom" block.  Wider clusters add no per-round traffic (only more block
+// transfers at the CTA boundaries) and put fewer warps on each SM, which
+// shortens a round: the host runs full waves of 2-CTA clusters and spreads a
+// remainder of slices (or a small batch) over 3 or 4 SMs per slice.  A round's 4 dot products per warp are then complete
 // after one warp butterfly (no cluster traffic, no wait), and the rotation
 // broadcast carries 4 pairs instead of 8.
 //
 // Ordering.  The same block tournament as the block-cyclic kernel over
 // nb = n_pad / 4 block positions, on nb / 2 warps numbered across the
-// cluster (CTA r holds warps r * nwa .. r * nwa + nwa - 1).  A block move
+// cluster (CTA r holds warps r nb / (2 CL) .. (r + 1) nb / (2 CL) - 1).  A block move
 // sends top blocks one warp up and bottom blocks one warp down, so a warp
 // depends only on its two neighbours: inside a CTA each block goes through
 // a mailbox slot guarded by a full / empty mbarrier pair (no CTA-wide
 // barrier), and warps drift against each other by up to a move.  Exactly
-// two blocks cross the CTA boundary per move (the top block of CTA 0's last
-// warp and the bottom block of CTA 1's first warp).  Each goes straight into
-// the peer's inbox with st.async (16-byte vectors), completing transaction
-// bytes on the inbox's mbarrier; the receiving warp waits for it (bounded)
-// and re-arms it for the use after next.  Inboxes alternate by move, and a
-// CTA can only write a peer's inbox again after receiving the peer's next
-// block, which the peer sends after emptying that inbox.  Blocks are stored
+// two blocks cross each CTA boundary per move (the top block of the lower
+// CTA's last warp and the bottom block of the upper CTA's first warp).  Each
+// goes straight into the neighbour's top or bottom inbox with st.async
+// (16-byte vectors), completing transaction bytes on that inbox's mbarrier;
+// the receiving warp waits for it (bounded) and re-arms it for the use after
+// next.  Inboxes alternate by move, and an edge warp can only write its
+// neighbour's inbox again after receiving the neighbour's next block, which
+// the neighbour's edge warp sends after emptying that inbox.  Blocks are stored
 // as 16-byte vectors of four rows, consecutive lanes 16 bytes apart
 // (conflict-free).
 //
@@ -40,9 +44,10 @@
 //
 // Per-sweep cluster agreement (the largest column norm for the
 // numerically-zero rule, and whether any pair still rotated) goes through a
-// two-entry DSMEM exchange and one cluster barrier each.
+// DSMEM exchange and one cluster barrier each.
 
 #include <atomic>
+#include <mutex>
 
 #include "jacobi_block.cuh"
 
@@ -58,8 +63,8 @@ using jblock::static_for;
 using jblock::try_wait_cluster;
 using jblock::wait_peers;
 
-constexpr int CL = 2;
-constexpr int NW = JAC_THREADS / 32;   // 16 warps per CTA
+constexpr int NW = JAC_THREADS / 32;   // at most 16 warps per CTA
+constexpr int kMaxCL = 4;
 constexpr int PPW = 4;                 // columns per block
 constexpr int RPL = 8;                 // rows per lane: 256 rows
 constexpr int HALF = PPW / 2;
@@ -81,21 +86,21 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 
 
 __host__ __device__ constexpr Layout layout(int n_pad) {
   Layout L{};
-  L.mbar = 0;                                                     // [2] u64: inboxes
-  L.full = L.mbar + 2 * 8;                                        // [2 NW] u64: slot filled
+  L.mbar = 0;                                                     // [2 sides][2] u64: inboxes
+  L.full = L.mbar + 4 * 8;                                        // [2 NW] u64: slot filled
   L.empty = L.full + 2 * size_t(NW) * 8;                          // [2 NW] u64: slot emptied
-  L.inbox = align16(L.empty + 2 * size_t(NW) * 8);                // [2][INBOX]
-  L.csa = align16(L.inbox + 2 * size_t(INBOX) * 4);               // [NW][2 PPW]
+  L.inbox = align16(L.empty + 2 * size_t(NW) * 8);                // [2 sides][2][INBOX]
+  L.csa = align16(L.inbox + 4 * size_t(INBOX) * 4);               // [NW][2 PPW]
   L.red = L.csa + size_t(NW) * 2 * PPW * 4;                       // [NW]
-  L.xch = L.red + size_t(NW) * 4;                                 // [2][CL]
-  L.mnorm = L.xch + 2 * CL * 4;                                   // [2 NW][PPW]
+  L.xch = L.red + size_t(NW) * 4;                                 // [2][kMaxCL]
+  L.mnorm = L.xch + 2 * kMaxCL * 4;                               // [2 NW][PPW]
   L.mscale = L.mnorm + 2 * size_t(NW) * PPW * 4;                  // [2 NW][PPW]
   L.norms = L.mscale + 2 * size_t(NW) * PPW * 4;                  // [n_pad]
   L.order = L.norms + size_t(n_pad) * 4;                          // [n_pad]
   L.rank_of = L.order + size_t(n_pad) * 4;                        // [n_pad]
   L.mail = align16(L.rank_of + size_t(n_pad) * 4);                // mailboxes / staging
   const size_t mail = 2 * size_t(NW) * BLK * 4;
-  const size_t stage = size_t(n_pad / 2) * kStagePitch * 4;
+  const size_t stage = size_t(2 * NW * PPW) * kStagePitch * 4;   // up to 16 warps' columns
   L.total = L.mail + (mail > stage ? mail : stage);
   return L;
 }
@@ -109,6 +114,7 @@ static __device__ __forceinline__ void st_async_v4(uint32_t remote_addr, float a
                : "memory");
 }
 
+template <int CL>
 __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Layout Ly = layout(a.n_pad);
@@ -127,23 +133,24 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
   float* mail = reinterpret_cast<float*>(smem_raw + Ly.mail);
 
   cg::cluster_group cluster = cg::this_cluster();
-  const int rank = int(cluster.block_rank()), peer = rank ^ 1;
+  const int rank = int(cluster.block_rank());
   const int slice = a.slice0 + int(blockIdx.x) / CL;
   const float* A = a.X + int64_t(slice) * a.n1 * a.n2;
   const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
   const int g = lane >> SHIFT, sub = lane & (LPP - 1);
   const int nb = a.n_pad / PPW;   // block positions
   const int nwt = nb / 2;         // warps over the cluster
-  const int nwa = nwt / 2;        // warps per CTA
+  const int start = rank * nwt / CL, end = (rank + 1) * nwt / CL;
+  const int nwa = end - start;    // warps of this CTA (at least 6)
   const bool active = warp < nwa;
-  const int W = rank * nwa + warp;                     // warp number in the cluster
+  const int W = start + warp;                          // warp number in the cluster
   const int topc = W * PPW, botc = (nb - 1 - W) * PPW; // first columns of its blocks
 
   // ---- stage this CTA's columns (two contiguous ranges), column-major with
   // an odd pitch: local column lc < nwa PPW is global topc0 + lc, the rest
   // are global botc0 + (lc - nwa PPW)
   const int nloc = 2 * nwa * PPW;
-  const int topc0 = rank * nwa * PPW, botc0 = (nb - (rank + 1) * nwa) * PPW;
+  const int topc0 = start * PPW, botc0 = (nb - end) * PPW;
   float* stg = mail;
   if (!a.trans) {
     for (int idx = threadIdx.x; idx < nloc * kMaxRows; idx += JAC_THREADS) {
@@ -163,10 +170,10 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
     }
   }
   if (threadIdx.x == 0) {
-    ptx::mbar_init(&mbar[0], 1);
-    ptx::mbar_init(&mbar[1], 1);
-    arm_tx(ptx::smem_u32(&mbar[0]), kInboxBytes);
-    arm_tx(ptx::smem_u32(&mbar[1]), kInboxBytes);
+    for (int i = 0; i < 4; ++i) {   // top inboxes [0, 2), bottom inboxes [2, 4)
+      ptx::mbar_init(&mbar[i], 1);
+      arm_tx(ptx::smem_u32(&mbar[i]), kInboxBytes);
+    }
     for (int i = 0; i < 2 * NW; ++i) {
       ptx::mbar_init(&full[i], 32);    // the posting warp's lanes
       ptx::mbar_init(&empty[i], 32);   // the fetching warp's lanes
@@ -190,29 +197,29 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
   // done before the mailboxes are reused
   cluster.sync();
 
-  const uint32_t inbox_peer = mapa_u32(ptx::smem_u32(inbox), peer);
-  const uint32_t mbar_peer = mapa_u32(ptx::smem_u32(mbar), peer);
-  float* xch_peer = cluster.map_shared_rank(xch, peer);
-  float* norms_peer = cluster.map_shared_rank(norms, peer);
-  // the two blocks that cross the cluster per move: CTA 0's last warp sends
-  // its top block and receives a bottom block; CTA 1's first warp sends its
-  // bottom block and receives a top block
-  const bool edge0 = active && rank == 0 && warp == nwa - 1;
-  const bool edge1 = active && rank == 1 && warp == 0;
+  // the blocks that cross a CTA boundary per move: a CTA's last warp sends
+  // its top block to the next CTA's top inbox and receives a bottom block
+  // (edge0); a CTA's first warp sends its bottom block to the previous CTA's
+  // bottom inbox and receives a top block (edge1)
+  const bool edge0 = active && rank < CL - 1 && warp == nwa - 1;
+  const bool edge1 = active && rank > 0 && warp == 0;
+  const int nbr = edge0 ? rank + 1 : edge1 ? rank - 1 : rank;
+  const uint32_t inbox_nbr = mapa_u32(ptx::smem_u32(inbox + (edge0 ? 0 : 2 * INBOX)), nbr);
+  const uint32_t mbar_nbr = mapa_u32(ptx::smem_u32(mbar + (edge0 ? 0 : 2)), nbr);
   uint32_t mv = 0;      // block moves so far (same count on both CTAs)
   bool failed = false;  // a bounded wait ran out: stop waiting
   uint32_t xu = 0;      // cluster exchanges so far
 
   // largest of a CTA-uniform value over the cluster
   auto cluster_max = [&](float v) {
-    const int s = int(xu & 1u) * CL;
-    if (threadIdx.x == 0) {
-      xch[s + rank] = v;
-      xch_peer[s + rank] = v;
-    }
+    const int s = int(xu & 1u) * kMaxCL;
+    if (threadIdx.x < CL) cluster.map_shared_rank(xch, int(threadIdx.x))[s + rank] = v;
     cluster.sync();
     ++xu;
-    return fmaxf(xch[s], xch[s + 1]);
+    float m = xch[s];
+#pragma unroll
+    for (int q = 1; q < CL; ++q) m = fmaxf(m, xch[s + q]);
+    return m;
   };
 
   float nT = 0.f, nB = 0.f;   // squared norms of top column g / bottom column paired with it
@@ -329,7 +336,7 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
   };
   auto send = [&](const float (&X)[PPW][RPL], float nrm, float d) {
     const uint32_t b = mv & 1u;
-    const uint32_t dst = inbox_peer + b * kInboxBytes, bar = mbar_peer + 8u * b;
+    const uint32_t dst = inbox_nbr + b * kInboxBytes, bar = mbar_nbr + 8u * b;
 #pragma unroll
     for (int j = 0; j < PPW; ++j)
 #pragma unroll
@@ -341,12 +348,13 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
       st_async_f32(dst + uint32_t(BLK + PPW + g) * 4u, d, bar);
     }
   };
-  auto receive = [&](float (&X)[PPW][RPL], float& nrm, float& d) {
+  // side 0: the top inbox (edge1 receives there), side 1: the bottom inbox (edge0)
+  auto receive = [&](float (&X)[PPW][RPL], float& nrm, float& d, int side) {
     const uint32_t b = mv & 1u, parity = (mv >> 1) & 1u;
-    const uint32_t bar = ptx::smem_u32(&mbar[b]);
+    const uint32_t bar = ptx::smem_u32(&mbar[2 * side + b]);
     if (!failed && !try_wait_cluster(bar, parity) && !wait_peers(bar, parity, a.status)) failed = true;
     failed = __any_sync(0xffffffffu, failed);   // one decision per warp
-    const float* src = inbox + b * INBOX;
+    const float* src = inbox + (2 * side + b) * INBOX;
     unpack(src, X);
     nrm = src[BLK + g];
     d = src[BLK + PPW + g];
@@ -489,12 +497,12 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
           nB = nT;
           dB = dT;
         } else if (edge0) {
-          receive(B, nB, dB);
+          receive(B, nB, dB, 1);
         } else {
           fetch(B, nB, dB, 2 * (warp + 1) + 1);
         }
         if (W >= 1) {
-          if (edge1) receive(T, nT, dT);
+          if (edge1) receive(T, nT, dT, 0);
           else fetch(T, nT, dT, W == 1 ? 1 : 2 * (warp - 1));
         }
       }
@@ -517,10 +525,12 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
     fold();
     exact_norms();
     if (sub == 0) {
-      norms[topc + g] = nT;
-      norms[botc + g] = nB;
-      norms_peer[topc + g] = nT;
-      norms_peer[botc + g] = nB;
+#pragma unroll
+      for (int q = 0; q < CL; ++q) {
+        float* nq = cluster.map_shared_rank(norms, q);
+        nq[topc + g] = nT;
+        nq[botc + g] = nB;
+      }
     }
   }
   cluster.sync();
@@ -564,6 +574,119 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
 }
 
 static std::atomic<int> g_enabled{1};
+static std::atomic<int> g_cluster{0};   // 0: automatic, else every launch on clusters of this size
+
+// Clusters of CL CTAs that can be resident at once (0 if the query fails).
+template <int CL>
+int max_clusters() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  if (cudaFuncSetAttribute(jacobi_cols_kernel<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(layout(kMaxPad).total)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(CL * 64), 1, 1);
+  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = layout(kMaxPad).total;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, jacobi_cols_kernel<CL>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached = n;
+  return n;
+}
+
+// `timed`: bracket the launch for per-kernel timing (a pair of launches is
+// timed as one span by launch_pair instead)
+template <int CL>
+int launch(const JacobiArgs& a, int nslices, cudaStream_t st, bool timed = true) {
+  if (nslices <= 0) return WP_OK;
+  if (max_clusters<CL>() <= 0) return WP_ERR_UNSUPPORTED;   // also sets the shared-memory attribute
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(nslices * CL), 1, 1);
+  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = layout(a.n_pad).total;
+  cfg.stream = st;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = CL;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 1;
+  if (timed) {
+    WP_PROFILE("jacobi_svd", st);
+    WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_cols_kernel<CL>, a));
+  } else {
+    WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_cols_kernel<CL>, a));
+  }
+  return launch_status();
+}
+
+static int launch_cl(int cl, const JacobiArgs& a, int nslices, cudaStream_t st, bool timed = true) {
+  return cl == 4 ? launch<4>(a, nslices, st, timed)
+                 : cl == 3 ? launch<3>(a, nslices, st, timed) : launch<2>(a, nslices, st, timed);
+}
+
+// Second stream and fork / join events of one device (created on first use,
+// kept for the life of the process), for two launches of different cluster
+// sizes that run side by side; the mutex keeps concurrent host threads from
+// interleaving their record / wait pairs on the shared events.
+struct Fork {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool ok = false;
+};
+static std::mutex g_fork_mu;
+
+static Fork* fork_of_device() {
+  static Fork forks[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  Fork& f = forks[dev];
+  if (!f.ok) {
+    if (cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    f.ok = true;
+  }
+  return &f;
+}
+
+// slices [slice0, slice0 + na) on clusters of cla CTAs on `st`, the next nb
+// beside them on clusters of clb CTAs on the side stream
+static int launch_pair(int cla, const JacobiArgs& a, int na, int clb, int nb, cudaStream_t st) {
+  JacobiArgs b = a;
+  b.slice0 = a.slice0 + na;
+  std::lock_guard<std::mutex> lk(g_fork_mu);
+  // one timed span on the call's stream, from before the fork to after the join
+  WP_PROFILE("jacobi_svd", st);
+  Fork* f = fork_of_device();
+  if (!f) {   // no second stream: one after the other
+    WP_TRY(launch_cl(cla, a, na, st, false));
+    return launch_cl(clb, b, nb, st, false);
+  }
+  WP_CUDA_TRY(cudaEventRecord(f->fork, st));
+  WP_CUDA_TRY(cudaStreamWaitEvent(f->side, f->fork, 0));
+  WP_TRY(launch_cl(cla, a, na, st, false));
+  WP_TRY(launch_cl(clb, b, nb, f->side, false));
+  WP_CUDA_TRY(cudaEventRecord(f->join, f->side));
+  WP_CUDA_TRY(cudaStreamWaitEvent(st, f->join, 0));
+  return WP_OK;
+}
 
 }  // namespace jcols
 
@@ -574,34 +697,32 @@ bool jacobi_cols_fits(int m_len, int n_vec) {
 
 bool jacobi_cols_enabled() { return jcols::g_enabled.load(std::memory_order_relaxed) != 0; }
 
+// Cluster sizes.  A slice takes 1, 0.81 and 0.66 of its 2-CTA time on 2-,
+// 3- and 4-CTA clusters (256 x 256 R^T factors on GB300), so 2-CTA clusters
+// do the most work per SM and wider ones pay off where SMs would otherwise
+// idle: (1) every slice in one wave of 4-CTA, else of 3-CTA clusters;
+// (2) a wave of 3-CTA clusters plus the few slices beyond its capacity on
+// 2-CTA clusters in the SMs it leaves, side by side; (3) full waves of
+// 2-CTA clusters and, beside them on the second stream, the remainder on
+// 3-CTA clusters (a last wave of a few 2-CTA clusters would leave most SMs
+// idle for a whole slice time).  3- and 4-CTA clusters do not share the
+// GPCs well (measured), so they are never paired.
 int jacobi_cols_launch(const JacobiArgs& a0, int nslices, cudaStream_t st) {
   if (!jacobi_cols_fits(a0.m_len, a0.n_vec)) return WP_ERR_UNSUPPORTED;
   JacobiArgs a = a0;
   a.n_pad = (a0.n_vec + 15) / 16 * 16;
   a.rpc = a0.m_len;
-  const size_t smem = jcols::layout(a.n_pad).total;
-  if (smem > 227 * 1024) return WP_ERR_UNSUPPORTED;
-  static bool attr = false;
-  if (!attr) {
-    WP_CUDA_TRY(cudaFuncSetAttribute(jcols::jacobi_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(jcols::layout(jcols::kMaxPad).total)));
-    attr = true;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(nslices * jcols::CL), 1, 1);
-  cfg.blockDim = dim3(JAC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attrs[1];
-  attrs[0].id = cudaLaunchAttributeClusterDimension;
-  attrs[0].val.clusterDim.x = jcols::CL;
-  attrs[0].val.clusterDim.y = 1;
-  attrs[0].val.clusterDim.z = 1;
-  cfg.attrs = attrs;
-  cfg.numAttrs = 1;
-  WP_PROFILE("jacobi_svd", st);
-  WP_CUDA_TRY(cudaLaunchKernelEx(&cfg, jcols::jacobi_cols_kernel, a));
-  return launch_status();
+  const int forced = jcols::g_cluster.load(std::memory_order_relaxed);
+  if (forced) return jcols::launch_cl(forced, a, nslices, st);
+  const int c2 = jcols::max_clusters<2>(), c3 = jcols::max_clusters<3>(), c4 = jcols::max_clusters<4>();
+  if (c2 <= 0) return WP_ERR_UNSUPPORTED;
+  if (nslices <= c4) return jcols::launch<4>(a, nslices, st);
+  if (nslices <= c3) return jcols::launch<3>(a, nslices, st);
+  const int spare2 = (sm_count() - 3 * c3) / 2;   // 2-CTA clusters beside a full wave of 3-CTA ones
+  if (c3 > 0 && nslices <= c3 + spare2) return jcols::launch_pair(3, a, c3, 2, nslices - c3, st);
+  const int full = nslices / c2 * c2, rest = nslices - full;
+  if (rest == 0 || c3 <= 0 || rest > c3) return jcols::launch<2>(a, nslices, st);
+  return jcols::launch_pair(2, a, full, 3, rest, st);
 }
 
 }  // namespace wp
@@ -610,4 +731,20 @@ extern "C" int wp_set_jacobi_column_split(int on) {
   if (on != 0 && on != 1) return WP_ERR_SHAPE;
   wp::jcols::g_enabled.store(on, std::memory_order_relaxed);
   return WP_OK;
+}
+
+extern "C" int wp_set_jacobi_cluster_size(int cl) {
+  if (cl != 0 && (cl < 2 || cl > wp::jcols::kMaxCL)) return WP_ERR_SHAPE;
+  wp::jcols::g_cluster.store(cl, std::memory_order_relaxed);
+  return WP_OK;
+}
+
+extern "C" int wp_jacobi_cluster_capacity(int cl, int* clusters) {
+  if (!clusters) return WP_ERR_NULL;
+  switch (cl) {
+    case 2: *clusters = wp::jcols::max_clusters<2>(); return WP_OK;
+    case 3: *clusters = wp::jcols::max_clusters<3>(); return WP_OK;
+    case 4: *clusters = wp::jcols::max_clusters<4>(); return WP_OK;
+    default: return WP_ERR_SHAPE;
+  }
 }

@@ -79,6 +79,10 @@ def test_limits_validated_on_the_host(libwprod):
     assert L.wp_set_jacobi_precondition(1) == 0            # the default
     assert L.wp_set_jacobi_column_split(-1) == 2           # on / off only
     assert L.wp_set_jacobi_column_split(1) == 0            # the default
+    assert L.wp_set_jacobi_cluster_size(1) == 2            # 0, 2, 3 or 4
+    assert L.wp_set_jacobi_cluster_size(5) == 2
+    assert L.wp_set_jacobi_cluster_size(0) == 0            # the default
+    assert L.wp_jacobi_cluster_capacity(2, None) == 1      # WP_ERR_NULL
     assert L.wp_selftest_bounded_wait(2, 1000000, None) == 2      # unknown wait kind
     assert L.wp_selftest_bounded_wait(0, 999, None) == 2          # limit below 1 us
     assert L.wp_selftest_bounded_wait(1, 100000001, None) == 2    # limit above 0.1 s

@@ -332,15 +332,20 @@ def test_qr_preconditioning_fewer_sweeps_same_result(n1, n2):
     assert capi.wp_get_device_error() == 0
 
 
-@pytest.mark.parametrize("n1,n2,pre", [(256, 256, True), (256, 250, True), (256, 200, False), (200, 256, False)])
-def test_jacobi_column_split_matches_row_split(n1, n2, pre):
+@pytest.mark.parametrize("n1,n2,pre,p", [(256, 256, True, 48), (256, 250, True, 48), (256, 200, False, 48),
+                                         (200, 256, False, 48), (256, 256, True, 16), (256, 256, True, 96),
+                                         (256, 256, True, 192)])
+def test_jacobi_column_split_matches_row_split(n1, n2, pre, p):
     """The column-split kernel (whole columns per CTA, 8 rows per lane) and
     the row-split block kernel compute the same one-sided Jacobi SVD in a
     different pair order: both meet the SVD bars against the oracle, on the
     QR path (R^T of 256 and of 250 columns, the latter padded to 256) and on
     tall and wide slices without it (200 columns padded to 208; the wide one
-    works on the transpose).  48 slices: 2-CTA clusters."""
-    p, L, r = 48, 3, 20
+    works on the transpose).  The slice counts take the automatic cluster
+    sizes' cases on a 152-SM GPU: 16 slices in one wave of 4-CTA clusters,
+    48 as a wave of 3-CTA clusters plus two 2-CTA clusters beside it, 96 and
+    192 as full waves of 2-CTA clusters plus the rest on 3-CTA clusters."""
+    L, r = 3, 20
     A = synth.hsi_cube(n1, n2, p, seed=4, dtype=np.float32)
     Ad = dev(A)
     res = {}
@@ -365,3 +370,24 @@ def test_jacobi_column_split_matches_row_split(n1, n2, pre):
         assert O.rel_fro(res[split][0], Cr) <= tol
     # same method: sweep counts within one per slice of each other
     assert abs(res[True][2][0] - res[False][2][0]) <= p
+
+
+@pytest.mark.parametrize("cl", [2, 3, 4])
+def test_jacobi_column_split_each_cluster_size(cl):
+    """Every launch of the column-split kernel forced onto clusters of 2, 3
+    or 4 CTAs (CTA boundaries at different warps, 1..3 boundaries): the same
+    SVD, within the bars, against the oracle; 24 slices of 256 x 256, R^T
+    path, ranks 20."""
+    p, L, r = 24, 3, 20
+    A = synth.hsi_cube(256, 256, p, seed=6, dtype=np.float32)
+    try:
+        capi.wp_set_jacobi_cluster_size(cl)
+        assert capi.wp_jacobi_cluster_capacity(cl) > 0
+        C, _, S, _ = capi.wp_wsvd(dev(A), L, r, factors=True)
+        torch.cuda.synchronize()
+        assert capi.wp_get_device_error() == 0
+    finally:
+        capi.wp_set_jacobi_cluster_size(0)
+    Cr, _, Sr, _ = O.wsvd(A, L, r, return_factors=True)
+    assert O.rel_fro(host(S), Sr) <= TOL_SIG
+    assert O.rel_fro(host(C), Cr) <= _rec_tol(A.astype(np.float64), L, r, p)
