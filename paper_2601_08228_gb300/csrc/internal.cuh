@@ -60,6 +60,10 @@ int jacobi_global_launch(const JacobiArgs& a, int nslices, void* work, size_t wo
 // Householder QR preconditioner of the Jacobi SVD (qr.cu): R^T (row-major)
 // of the working matrix of each of slices [0, nslices) of X (p, n1, n2).
 bool qr_supported(int m_len, int n_vec);
+// Register-resident cluster QR (qr_cols.cu) of working matrices of at most
+// 256 x 256: writes R^T row-major (nslices, n, n) to R like qr_r.
+bool qr_cols_fits(int m_len, int n_vec);
+int qr_cols_launch(const float* X, int n1, int n2, int nslices, float* R, cudaStream_t st);
 size_t qr_work_bytes(int m_len, int n_vec, int nslices);
 int qr_r(const float* X, int n1, int n2, int nslices, void* work, size_t work_bytes, float** Rt_out,
          cudaStream_t st);

@@ -10,7 +10,9 @@
 // give the right singular vectors of X (U_R) and its singular values; Q is
 // never formed.
 //
-// One CTA per slice.  The working matrix is copied column-major into a work
+// Working matrices of at most 256 x 256 go to the register-resident cluster
+// kernel of qr_cols.cu instead.  Larger ones: one CTA per slice.  The working
+// matrix is copied column-major into a work
 // buffer (each column contiguous, L2-resident) and factored in panels of
 // QR_B columns: one warp factors the panel in shared memory with Householder
 // reflections H_c = I - tau_c v_c v_c^T (v_c[c] = 1; beta_c = -sign(alpha)
@@ -302,6 +304,13 @@ int qr_r(const float* X, int n1, int n2, int nslices, void* work, size_t work_by
   float* W = cv.take<float>(size_t(nslices) * n * m);
   float* R = cv.take<float>(size_t(nslices) * n * n);
   if (!cv.ok) return WP_ERR_WORKSPACE;
+  // working matrices of at most 256 x 256: factored in registers on a cluster
+  // (qr_cols.cu); W is not used then
+  if (qr_cols_fits(m, n)) {
+    WP_TRY(qr_cols_launch(X, n1, n2, nslices, R, st));
+    *R_out = R;
+    return WP_OK;
+  }
   // panel, T, tau, beta, z + per-warp y; at least the per-warp 32 x 33 staging tiles
   auto floats = [](int mm, int threads) {
     return std::max<size_t>(size_t(QR_B) * mm + QR_B * QR_B + 2 * QR_B + ((threads / 32) * QR_CB + 1) * QR_B,

@@ -274,3 +274,57 @@ def test_blocked_qr_restatement(m, n):
     np.testing.assert_allclose(R * sgn[:, None], Rref, atol=1e-10 * np.abs(Rref).max())
     np.testing.assert_allclose(np.linalg.svd(R, compute_uv=False), np.linalg.svd(X, compute_uv=False), rtol=1e-10,
                                atol=1e-12)
+
+
+def _panel4_qr_rt(X):
+    """Restatement of qr_cols_kernel's arithmetic (fp64): 4-column panels,
+    each factored column by column (H_c = I - tau v v^T, v[k] = 1, beta =
+    -sign(alpha)|x|), T from the panel's Gram entries, the trailing columns
+    updated with Y = V^T C, Y' = T^T Y, C -= V Y'; returns R^T as written."""
+    PB, ROWS = 4, 256
+    m, n = X.shape
+    nbk = (n + PB - 1) // PB
+    Xp = np.zeros((ROWS, nbk * PB))
+    Xp[:m, :n] = X
+    rows = np.arange(ROWS)
+    for b in range(nbk):
+        k0 = b * PB
+        P = Xp[:, k0:k0 + PB]
+        tau = np.zeros(PB)
+        for c in range(PB):
+            k = k0 + c
+            alpha, s2 = P[k, c], np.sum(P[rows > k, c] ** 2)
+            t, beta, scl = 0.0, alpha, 0.0
+            if s2 > 0:
+                nrm = np.sqrt(alpha * alpha + s2)
+                beta = -nrm if alpha >= 0 else nrm
+                t, scl = (beta - alpha) / beta, 1 / (alpha - beta)
+            tau[c] = t
+            P[rows > k, c] *= scl
+            v = np.where(rows > k, P[:, c], np.where(rows == k, 1.0, 0.0))
+            for c2 in range(c + 1, PB):
+                P[:, c2] -= (v @ P[:, c2]) * t * v
+            P[k, c] = beta
+        V = np.stack([np.where(rows > k0 + c, P[:, c], np.where(rows == k0 + c, 1.0, 0.0)) for c in range(PB)], 1)
+        G = V.T @ V
+        T = np.zeros((PB, PB))
+        for c in range(PB):
+            T[c, c] = tau[c]
+            for l in range(c):
+                T[l, c] = -tau[c] * sum(T[l, q] * G[q, c] for q in range(l, c))
+        for c in range(PB):
+            P[rows > k0 + c, c] = 0.0
+        C = Xp[:, k0 + PB:]
+        Xp[:, k0 + PB:] = C - V @ (T.T @ (V.T @ C))
+    return Xp[:n, :n].T.copy()
+
+
+@pytest.mark.parametrize("m,n", [(256, 256), (256, 250), (200, 193), (256, 64), (37, 5)])
+def test_panel4_qr_restatement(m, n):
+    """The register-resident cluster QR's steps reproduce R of X = QR: upper
+    triangular, |R| equal to LAPACK's, R^T R = X^T X."""
+    X = np.random.default_rng(m + n).standard_normal((m, n))
+    R = _panel4_qr_rt(X).T
+    assert np.allclose(np.tril(R, -1), 0)
+    np.testing.assert_allclose(np.abs(R), np.abs(np.linalg.qr(X, mode="r")), atol=1e-9)
+    np.testing.assert_allclose(R.T @ R, X.T @ X, atol=1e-8)
