@@ -870,6 +870,25 @@ def _extras(capi, args):
     if "gemm_tflops" in study["fp8"] and fp8.get("tflops"):
         study["fp8"]["gemm_frac"] = study["fp8"]["gemm_tflops"] / fp8["tflops"]
         study["fp8"]["gemm_peak"] = f"measured FP8 {fp8['tflops']:.0f} ({fp8['how']})"
+    # each face-product kernel against its own roofline: it reads both operands
+    # once (bytes per element: BF16 2, BF16x3 hi + lo 4, E4M3 1) and writes C
+    # (FP32) once; ceiling = min(tensor peak / products per output, intensity x HBM)
+    per_slice_elems = 1024 * 1024 + 1024 * 512
+    for prec, ebytes, nprod, tpeak in (("bf16", 2, 1, peaks["bf16_tflops"]), ("bf16x3", 4, 3, peaks["bf16_tflops"]),
+                                       ("fp8", 1, 1, fp8.get("tflops"))):
+        if "gemm_tflops" not in study[prec] or not tpeak:
+            continue
+        gbytes = 256.0 * (per_slice_elems * ebytes + 1024 * 512 * 4)
+        inten = flops / gbytes
+        ceil_ = min(tpeak / nprod, inten * peaks["hbm_gbs"] / 1e3)
+        study[prec]["gemm_bytes"] = gbytes
+        study[prec]["gemm_flop_per_byte"] = inten
+        study[prec]["gemm_roofline_tflops"] = ceil_
+        study[prec]["gemm_frac_of_roofline"] = study[prec]["gemm_tflops"] / ceil_
+        study[prec]["gemm_roofline_bound"] = "tensor" if tpeak / nprod <= inten * peaks["hbm_gbs"] / 1e3 else "hbm"
+        if nprod > 1:
+            study[prec]["tensor_issued_tflops"] = nprod * study[prec]["gemm_tflops"]
+            study[prec]["tensor_issued_frac"] = nprod * study[prec]["gemm_tflops"] / tpeak
     out["fp8_peak"] = fp8
     out["precision_1024x1024x256_by_1024x512x256_L4"] = study
     return out
