@@ -391,3 +391,33 @@ def test_jacobi_column_split_each_cluster_size(cl):
     Cr, _, Sr, _ = O.wsvd(A, L, r, return_factors=True)
     assert O.rel_fro(host(S), Sr) <= TOL_SIG
     assert O.rel_fro(host(C), Cr) <= _rec_tol(A.astype(np.float64), L, r, p)
+
+
+def test_wsvd_cuda_graph_with_paired_jacobi():
+    """192 slices of 256 x 256: the QR on 2-CTA clusters and the Jacobi as
+    two launches side by side, the second on the library's own stream,
+    forked from and joined back to the call's stream with events.  The call
+    captured in a CUDA graph (after one eager call, which sets up the side
+    stream and the kernels' attributes) and replayed twice gives the eager
+    result bit for bit."""
+    import ctypes
+    p, L, r = 192, 3, 20
+    A = dev(synth.hsi_cube(256, 256, p, seed=2, dtype=np.float32))
+    nb = ctypes.c_size_t(0)
+    assert capi.lib().wp_wsvd_workspace(256, 256, p, L, r, ctypes.byref(nb)) == 0
+    ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        eager = capi.wp_wsvd(A, L, r, ws=ws)
+    s.synchronize()
+    eager = host(eager)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        Cg = capi.wp_wsvd(A, L, r, ws=ws)
+    for _ in range(2):
+        Cg.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(Cg), eager)
+    assert capi.wp_get_device_error() == 0
