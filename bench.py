@@ -707,7 +707,8 @@ def _extras(capi, args):
     torch.cuda.synchronize()
     t = a.elapsed_time(b) / 1e3 / reps
     out["batched_4096"] = {"tensors_per_s": 4096 / t, "ms": t * 1e3, "graph": True,
-                           "gemm_threads": bl.plan.gemm_threads, "svd_threads": bl.plan.svd_threads}
+                           "gemm_threads": bl.plan.gemm_threads, "svd_threads": bl.plan.svd_threads,
+                           "svd_kernel": "lane-group" if bl.plan.svd_group else "block-cyclic"}
     del dev, bl, g
     # the w-svd and sp-w-svd of the workload with the Jacobi SVD's QR preconditioning switched
     # off (the timed steps run with it on): time and sweeps per slice of both variants

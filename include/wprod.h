@@ -475,6 +475,9 @@ typedef struct {
   int64_t n_units_mid;                 /* the next n_units_mid 32 < min(n1, n2) <= 48 */
   int64_t lift_fwd_blocks, lift_inv_blocks;
   uint64_t items_off, lift_fwd_off, lift_inv_off, units_off;
+  int32_t svd_group;                   /* 1: lane-group Jacobi kernel for every slice class, 0: block-cyclic
+                                          (autotuned when tune = 1; 1 otherwise) */
+  int32_t reserved;
 } wp_batch_plan;
 
 /* `items` is a HOST array of `count` descriptors (device pointers inside).

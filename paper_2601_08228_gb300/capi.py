@@ -48,7 +48,7 @@ class WPBatchPlan(ctypes.Structure):
                 ("svd_vec_floats", ctypes.c_int32), ("n_units", ctypes.c_int64), ("n_units_narrow", ctypes.c_int64), ("n_units_mid", ctypes.c_int64),
                 ("lift_fwd_blocks", ctypes.c_int64), ("lift_inv_blocks", ctypes.c_int64),
                 ("items_off", ctypes.c_uint64), ("lift_fwd_off", ctypes.c_uint64), ("lift_inv_off", ctypes.c_uint64),
-                ("units_off", ctypes.c_uint64)]
+                ("units_off", ctypes.c_uint64), ("svd_group", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class WPLiftOps(ctypes.Structure):

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "internal.cuh"
 #include "jacobi_block.cuh"
+#include "jacobi_group.cuh"
 #include "jacobi_common.cuh"
 #include "lift_math.cuh"
 
@@ -200,22 +201,25 @@ __global__ void batched_facewise_kernel(const BItem* __restrict__ items, const i
 // work list): blocks of PPW columns, NW warps, rows lane and lane + 32 of
 // every column in registers (slices up to 64 x 64), then the rank-r rebuild
 // from the leading vectors, staged in shared memory.
-template <int PPW, int NW>
+template <int PPW, int NW, bool GROUP = false>
 struct BJ {
   static constexpr int RPL = 2;
-  static constexpr size_t BLOCK = jblock::block_smem<1, PPW, RPL, NW>(BMAX);   // n_pad <= 64
+  static constexpr size_t BLOCK = GROUP ? jgroup::Lay<NW>::total
+                                        : jblock::block_smem<1, PPW, RPL, NW>(BMAX);   // n_pad <= 64
   // + the leading vectors, max(n1, n2) x r floats (at most 64 x 64)
   static size_t smem(int vec_floats) { return BLOCK + (size_t(vec_floats) * sizeof(float) + 15) / 16 * 16; }
 };
 
 // 64 registers: 1024 threads per SM's worth of CTAs (8 of 4 warps, 4 of 8)
 // when shared memory allows.
-template <int PPW, int NW>
+// GROUP: the lane-group kernel of jacobi_group.cuh (blocks of 4 columns)
+// instead of the block-cyclic one.
+template <int PPW, int NW, bool GROUP>
 __global__ void __launch_bounds__(NW * 32, 32 / NW) batched_jacobi_kernel(const BItem* __restrict__ items,
                                                                  const int2* __restrict__ units, int64_t nunits,
                                                                  int max_sweeps, int* status,
                                                                  unsigned long long* stats) {
-  using L = BJ<PPW, NW>;
+  using L = BJ<PPW, NW, GROUP>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* vec = reinterpret_cast<float*>(smem_raw + L::BLOCK);   // m_len x r
   float* T = reinterpret_cast<float*>(smem_raw);                // rebuild scratch (block area is free by then)
@@ -238,7 +242,8 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) batched_jacobi_kernel(const 
     b.status = status;
     b.stats = stats;
     const float* A = it.Ah + int64_t(uk.y) * n1 * n2;
-    jblock::block_jacobi_slice<1, PPW, L::RPL, NW, false>(b, A, 0, vec, nullptr);
+    if constexpr (GROUP) jgroup::group_jacobi_slice<NW>(b, A, vec);
+    else jblock::block_jacobi_slice<1, PPW, L::RPL, NW, false>(b, A, 0, vec, nullptr);
     // rebuild the rank-r slice from the original A_hat_k (still in global memory)
     float* Cr = it.Crh + int64_t(uk.y) * n1 * n2;
     if (!b.trans) {
@@ -364,23 +369,23 @@ static int launch_batched_gemm(const BItem* items, const int2* units, int64_t n,
   return launch_status();
 }
 
-template <int PPW, int NW>
+template <int PPW, int NW, bool GROUP = false>
 static int launch_batched_jacobi_t(const BItem* items, const int2* units, int64_t n, int vec_floats,
                                    cudaStream_t st) {
-  using L = BJ<PPW, NW>;
+  using L = BJ<PPW, NW, GROUP>;
   const size_t smem = L::smem(vec_floats);
   static bool attr = false;
   if (!attr) {
-    WP_CUDA_TRY(cudaFuncSetAttribute(batched_jacobi_kernel<PPW, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WP_CUDA_TRY(cudaFuncSetAttribute(batched_jacobi_kernel<PPW, NW, GROUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(L::smem(BMAX * BMAX))));
     attr = true;
   }
   int per_sm = 0;
-  WP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_jacobi_kernel<PPW, NW>, NW * 32, smem));
+  WP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_jacobi_kernel<PPW, NW, GROUP>, NW * 32, smem));
   if (per_sm < 1) per_sm = 1;
   const int64_t grid = std::min<int64_t>(n, int64_t(sm_count()) * per_sm);
   WP_PROFILE("batched_jacobi", st);
-  batched_jacobi_kernel<PPW, NW><<<unsigned(std::max<int64_t>(grid, 1)), NW * 32, smem, st>>>(
+  batched_jacobi_kernel<PPW, NW, GROUP><<<unsigned(std::max<int64_t>(grid, 1)), NW * 32, smem, st>>>(
       items, units, n, jacobi_max_sweeps(), device_status_ptr(), jacobi_stats_ptr());
   return launch_status();
 }
@@ -389,8 +394,9 @@ static int launch_batched_jacobi_t(const BItem* items, const int2* units, int64_
 // Slices with min(n1, n2) > 32 (up to 64 columns): 8 warps of 4-column
 // blocks or 4 warps of 8-column blocks, as tuned.
 static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t n, int threads, int vec_floats,
-                                 cudaStream_t st) {
+                                 bool group, cudaStream_t st) {
   if (n < 1) return WP_OK;
+  if (group) return launch_batched_jacobi_t<4, 8, true>(items, units, n, vec_floats, st);
   if (threads == 256) return launch_batched_jacobi_t<4, 8>(items, units, n, vec_floats, st);
   return launch_batched_jacobi_t<8, 4>(items, units, n, vec_floats, st);
 }
@@ -399,14 +405,16 @@ static int launch_batched_jacobi(const BItem* items, const int2* units, int64_t 
 // that at most one warp of a CTA idles and more slices run per SM than on
 // 8-warp CTAs.
 static int launch_batched_jacobi_narrow(const BItem* items, const int2* units, int64_t n, int vec_floats,
-                                        cudaStream_t st) {
+                                        bool group, cudaStream_t st) {
   if (n < 1) return WP_OK;
+  if (group) return launch_batched_jacobi_t<4, 4, true>(items, units, n, vec_floats, st);
   return launch_batched_jacobi_t<4, 4>(items, units, n, vec_floats, st);
 }
 
-static int launch_batched_jacobi_mid(const BItem* items, const int2* units, int64_t n, int vec_floats,
+static int launch_batched_jacobi_mid(const BItem* items, const int2* units, int64_t n, int vec_floats, bool group,
                                      cudaStream_t st) {
   if (n < 1) return WP_OK;
+  if (group) return launch_batched_jacobi_t<4, 6, true>(items, units, n, vec_floats, st);
   return launch_batched_jacobi_t<4, 6>(items, units, n, vec_floats, st);
 }
 
@@ -529,6 +537,8 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
   plan->n_units_mid = n_mid;
   plan->gemm_threads = 256;
   plan->svd_threads = 128;
+  plan->svd_group = 1;
+  plan->reserved = 0;
   plan->svd_vec_floats = 1;
   for (int i = 0; i < count; ++i)
     plan->svd_vec_floats = std::max(plan->svd_vec_floats, std::max(items[i].n1, items[i].n2) * items[i].r);
@@ -543,12 +553,23 @@ extern "C" int wp_batched_plan(const wp_batch_item* items, int count, int tune, 
       const float t = time_candidate([&] { launch_batched_gemm(di, du, lay.nunits, thr, st); }, st);
       if (t < best) { best = t; plan->gemm_threads = thr; }
     }
+    // the whole Jacobi phase: the lane-group kernel, or the block-cyclic one
+    // with either CTA size for the widest class
     best = 1e30f;
-    for (int thr : {128, 256}) {
-      const float t =
-          time_candidate([&] { launch_batched_jacobi(di, du + n_narrow + n_mid, lay.nunits - n_narrow - n_mid, thr,
-                                                     plan->svd_vec_floats, st); }, st);
-      if (t < best) { best = t; plan->svd_threads = thr; }
+    for (int cand = 0; cand < 3; ++cand) {
+      const bool grp = cand == 0;
+      const int thr = cand == 2 ? 256 : 128;
+      const float t = time_candidate([&] {
+        launch_batched_jacobi_narrow(di, du, n_narrow, plan->svd_vec_floats, grp, st);
+        launch_batched_jacobi_mid(di, du + n_narrow, n_mid, plan->svd_vec_floats, grp, st);
+        launch_batched_jacobi(di, du + n_narrow + n_mid, lay.nunits - n_narrow - n_mid, thr, plan->svd_vec_floats,
+                              grp, st);
+      }, st);
+      if (t < best) {
+        best = t;
+        plan->svd_group = grp ? 1 : 0;
+        plan->svd_threads = thr;
+      }
     }
     WP_CUDA_TRY(cudaGetLastError());
   }
@@ -559,6 +580,7 @@ extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream)
   if (!plan || !ws) return WP_ERR_NULL;
   if (plan->count < 1 || plan->n_units < 1) return WP_ERR_SHAPE;
   if (plan->svd_vec_floats < 1 || plan->svd_vec_floats > BMAX * BMAX) return WP_ERR_SHAPE;
+  if (plan->svd_group != 0 && plan->svd_group != 1) return WP_ERR_SHAPE;
   if (plan->n_units_narrow < 0 || plan->n_units_mid < 0 ||
       plan->n_units_narrow + plan->n_units_mid > plan->n_units)
     return WP_ERR_SHAPE;
@@ -576,10 +598,11 @@ extern "C" int wp_batched_run(const wp_batch_plan* plan, void* ws, void* stream)
   WP_CUDA_TRY(cudaStreamWaitEvent(f->side, f->fork, 0));
   WP_TRY(launch_batched_gemm(di, du, plan->n_units, plan->gemm_threads, f->side));
   const int64_t nn = plan->n_units_narrow, nm = plan->n_units_mid;
-  WP_TRY(launch_batched_jacobi_narrow(di, du, nn, plan->svd_vec_floats, st));
-  WP_TRY(launch_batched_jacobi_mid(di, du + nn, nm, plan->svd_vec_floats, st));
+  const bool grp = plan->svd_group != 0;
+  WP_TRY(launch_batched_jacobi_narrow(di, du, nn, plan->svd_vec_floats, grp, st));
+  WP_TRY(launch_batched_jacobi_mid(di, du + nn, nm, plan->svd_vec_floats, grp, st));
   WP_TRY(launch_batched_jacobi(di, du + nn + nm, plan->n_units - nn - nm, plan->svd_threads, plan->svd_vec_floats,
-                               st));
+                               grp, st));
   WP_CUDA_TRY(cudaEventRecord(f->join, f->side));
   WP_CUDA_TRY(cudaStreamWaitEvent(st, f->join, 0));
   return launch_batched_lift(reinterpret_cast<const LiftDesc*>(base + plan->lift_inv_off), plan->n_lift_inv,

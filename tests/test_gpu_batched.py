@@ -58,6 +58,22 @@ def test_batched_small_every_item():
     assert capi.wp_get_device_error() == 0
 
 
+@pytest.mark.parametrize("group,threads", [(1, 128), (0, 128), (0, 256)])
+def test_batched_both_jacobi_kernels(group, threads):
+    """The Jacobi phase on the lane-group kernel (the default plan) and on
+    the block-cyclic kernel with either CTA size for the widest class:
+    every item of a mixed batch against the oracle."""
+    items = synth.batch_items(count=40, seed=9)
+    dev = _device_items(items, 6)
+    bl = capi.BatchedLaunch(dev)
+    assert bl.plan.svd_group == 1
+    bl.plan.svd_group = group
+    bl.plan.svd_threads = threads
+    bl.run()
+    _check_items(items, dev, range(len(items)), 6)
+    assert capi.wp_get_device_error() == 0
+
+
 def test_batched_rank_above_min_dims_rejected():
     items = synth.batch_items(count=4, seed=5)
     dev = _device_items(items, 8)
