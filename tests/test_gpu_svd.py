@@ -421,3 +421,21 @@ def test_wsvd_cuda_graph_with_paired_jacobi():
         torch.cuda.synchronize()
         np.testing.assert_array_equal(host(Cg), eager)
     assert capi.wp_get_device_error() == 0
+
+
+@pytest.mark.parametrize("n1,n2", [(200, 193), (193, 200), (130, 77), (256, 33), (250, 250)])
+def test_qr_preconditioned_ragged_shapes(n1, n2):
+    """The register-resident cluster QR on working matrices whose column
+    count is not a multiple of its 4-column panels (193, 77, 33, 250: zero
+    padding columns), with fewer than 256 rows, and wide slices (the QR of
+    the transpose); the Jacobi then takes R^T on the column-split kernel
+    (193, 250 columns) or the row-split one (77, 33).  Singular values and
+    the rank-r reconstruction against the oracle."""
+    p, L, r = 16, 2, 10
+    A = synth.hsi_cube(n1, n2, p, seed=12, dtype=np.float32)
+    C, _, S, _ = capi.wp_wsvd(dev(A), L, r, factors=True)
+    torch.cuda.synchronize()
+    Cr, _, Sr, _ = O.wsvd(A, L, r, return_factors=True)
+    assert O.rel_fro(host(S), Sr) <= TOL_SIG
+    assert O.rel_fro(host(C), Cr) <= _rec_tol(A.astype(np.float64), L, r, p)
+    assert capi.wp_get_device_error() == 0
