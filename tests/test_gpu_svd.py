@@ -439,3 +439,28 @@ def test_qr_preconditioned_ragged_shapes(n1, n2):
     assert O.rel_fro(host(S), Sr) <= TOL_SIG
     assert O.rel_fro(host(C), Cr) <= _rec_tol(A.astype(np.float64), L, r, p)
     assert capi.wp_get_device_error() == 0
+
+
+@pytest.mark.parametrize("r", [3, 6])
+@pytest.mark.parametrize("sparse", [False, True])
+def test_qr_preconditioned_rank_deficient(r, sparse):
+    """Exactly low-rank slices on the QR path: a noise-free rank-3 cube
+    (rank 4 in the approximation slices with the normalisation's constant),
+    so R has only a few rows above rounding level and R^T as many
+    numerically-zero columns, which the Jacobi must leave alone (numerically
+    zero rule) and still converge.  Ranks inside and beyond the numerical
+    rank; w-svd and sp-w-svd; 48 slices of 256 x 256 (the column-split
+    kernel's cluster policy)."""
+    p, L = 48, 3
+    A = synth.hsi_cube(256, 256, p, rank=3, noise=0.0, seed=13, dtype=np.float32)
+    capi.wp_jacobi_stats()
+    C, _, S, _ = capi.wp_wsvd(dev(A), L, r, sparse=sparse, factors=True)
+    torch.cuda.synchronize()
+    total, mx = capi.wp_jacobi_stats()
+    fn = O.spwsvd if sparse else O.wsvd
+    Cr, _, Sr, _ = fn(A, L, r, return_factors=True)
+    assert 0 < mx < 40                    # converged well inside the default sweep limit
+    nsl = min(2 * (p >> L), p) if sparse else p
+    assert O.rel_fro(host(S), Sr) <= TOL_SIG
+    assert O.rel_fro(host(C), Cr) <= max(1e-5, _rec_tol(A.astype(np.float64), L, r, nsl))
+    assert capi.wp_get_device_error() == 0
