@@ -14,10 +14,10 @@
 // Two kernels share these definitions.  The block-cyclic register-resident
 // kernel (jacobi_block.cu) takes every slice with more than 32 columns whose
 // rows fit in registers on at most 8 CTAs; the shared-memory kernel below
-// takes the rest (narrow slices, very tall ones).  The block kernel also ends
-// the iteration after a sweep whose largest cosine stays below 0.3 sqrt(tol):
-// by the quadratic convergence of the method the next sweep would find no
-// pair above tol, so it is not run.
+// takes the rest (narrow slices, very tall ones).  The register-resident
+// kernels also end the iteration after a sweep whose largest cosine stays
+// below sqrt(tol): by the quadratic convergence of the method the next sweep
+// would leave cosines of order tol, so it is not run.
 //
 // Shared-memory kernel.  Parallel ordering: round-robin "circle" tournament,
 // n_pad - 1 rounds of n_pad / 2 disjoint pairs per sweep.  A slice is held in

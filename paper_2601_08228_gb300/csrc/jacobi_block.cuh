@@ -361,10 +361,10 @@ __device__ __forceinline__ void block_jacobi_slice(const JacobiArgs& a, const fl
     const float negl = nmax * meps * meps;
     // Stopping rule.  A sweep in which no pair's cosine |gamma| / sqrt(alpha
     // beta) reaches tol ends the iteration.  Jacobi converges quadratically
-    // near the end, so a sweep whose largest cosine stays below 0.3 sqrt(tol)
-    // leaves cosines of order 0.09 tol: it ends the iteration too, without
-    // the confirming sweep that would find nothing to rotate.
-    tol2s = 0.09f * tol_eff;
+    // near the end, so a sweep whose largest cosine stays below sqrt(tol)
+    // leaves cosines of order tol: it ends the iteration too, without the
+    // confirming sweep that would find (next to) nothing to rotate.
+    tol2s = tol_eff;
     big = 0;
 
     if (active) {

@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(JAC_THREADS, 1) jacobi_cols_kernel(JacobiArgs 
     const float meps = float(a.m_len) * 1.1920929e-7f;
     const float negl = nmax * meps * meps;
     // stopping rule of the block-cyclic kernel: no cosine above tol, or none
-    // above 0.3 sqrt(tol) (the next sweep would find nothing to rotate)
-    tol2s = 0.09f * tol_eff;
+    // above sqrt(tol) (the next sweep would find nothing above tol to rotate)
+    tol2s = tol_eff;
     big = 0;
 
     if (active) {

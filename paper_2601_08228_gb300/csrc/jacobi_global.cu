@@ -19,8 +19,9 @@
 // (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t, rotated when
 // |gamma| > tol sqrt(alpha beta); columns below (m_len eps)^2 max |x|^2 are
 // numerically zero and never rotated.  A sweep in which no pair's cosine
-// |gamma| / sqrt(alpha beta) reaches 0.3 sqrt(tol) ends the iteration of
-// that slice (quadratic convergence: the next sweep would rotate nothing).
+// |gamma| / sqrt(alpha beta) reaches sqrt(tol) ends the iteration of that
+// slice (quadratic convergence: the next sweep would leave cosines of order
+// tol).
 //
 // The kernel is persistent and launched cooperatively (all CTAs resident):
 // the CTAs take the work items of a round in turn and meet at a grid-wide
@@ -108,7 +109,7 @@ __device__ __forceinline__ bool rotate_pair(float* x, float* y, int m, float tol
   ga = warp_sum(ga);
   if (!(al > negl && be > negl) || ga == 0.f) return false;
   const float ab = al * be;
-  const bool big = ga * ga > 0.09f * tol * ab;
+  const bool big = ga * ga > tol * ab;
   if (fabsf(ga) <= tol * sqrtf(ab)) return big;
   const float zeta = __fdividef(be - al, 2.f * ga);
   const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));

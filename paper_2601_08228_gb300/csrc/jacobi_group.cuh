@@ -200,7 +200,7 @@ __device__ __forceinline__ void group_jacobi_slice(const JacobiArgs& a, const fl
     for (int w = 0; w < NW; ++w) nmax = fmaxf(nmax, red[w]);
     const float meps = float(a.m_len) * 1.1920929e-7f;
     const float negl = nmax * meps * meps;
-    tol2s = 0.09f * tol_eff;
+    tol2s = tol_eff;
     big = 0;
 
     if (active) {
