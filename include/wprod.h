@@ -160,9 +160,11 @@ WP_API int wp_set_jacobi_column_split(int on);
  * remaining slices beside them on 3-CTA clusters when they fit one wave of
  * those.  Two such parts run side by side: the second on a library-owned
  * stream of the device, forked from and joined back to the call's stream
- * with events (both are captured when the call's stream is).  2, 3 or 4
- * puts every launch on clusters of that size, on the call's stream.  Else
- * WP_ERR_SHAPE.  Process-wide. */
+ * with events (both are captured when the call's stream is); calls from
+ * several host threads on one device share that stream, so their second
+ * parts run one after another (the enqueueing is serialised by a lock).
+ * 2, 3 or 4 puts every launch on clusters of that size, on the call's
+ * stream.  Else WP_ERR_SHAPE.  Process-wide. */
 WP_API int wp_set_jacobi_cluster_size(int cl);
 
 /* Number of clusters of `cl` CTAs (2, 3 or 4, else WP_ERR_SHAPE) of the
