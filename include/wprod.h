@@ -431,10 +431,15 @@ WP_API int wp_deblur_pinv(const float* AV, const float* AH, const float* B, floa
  * order; with 0 they are mapped to the spatial domain with W^{-1} (Thm 2.5).
  * Singular vectors are determined up to sign.
  * Size limit: a slice's working matrix (max(n1, n2) rows, min(n1, n2)
- * columns) must fit on one 8-CTA thread-block cluster -- in shared memory
- * (about n_cols * rows / 8 <= 51200 floats, e.g. 640 x 640) or in registers
- * (up to 512 columns and 8 x 64 rows); other shapes return
- * WP_ERR_UNSUPPORTED (the same limit holds for wp_wpinv). */
+ * columns) is held on one thread-block cluster (in registers or shared
+ * memory) when it fits one, and otherwise in a global-memory work buffer
+ * (part of the workspace) with two column blocks of the long side staged
+ * in shared memory: up to 6400 rows; longer ones return WP_ERR_UNSUPPORTED
+ * (the same limits hold for wp_wpinv).
+ * Range: column norms and dot products are FP32 sums of products, so
+ * slices whose entries all lie below about 1e-19 or above about 1e19 in
+ * magnitude (squares under- or overflowing FP32) lose their small or large
+ * columns; scale such tensors first (the SVD of cA is c times that of A). */
 WP_API int wp_wsvd_workspace(int64_t n1, int64_t n2, int64_t p, int L, int r, size_t* bytes);
 WP_API int wp_wsvd(const float* A, float* C_r, float* U, float* S, float* V, int64_t n1, int64_t n2,
             int64_t p, int L, int r, int sparse, int factors_in_wavelet_domain, void* ws,
