@@ -280,25 +280,29 @@ WP_API int wp_gwprod_backward(const float* A, const float* B, const float* G, fl
 
 /* ---- autotuner and plan cache of the tensor-core w-product -------------- */
 
-/* The BF16 / BF16X3 w-product without transposes (1 <= L <= 5) has two
+/* The BF16 / BF16X3 w-product without transposes (1 <= L <= 5) has three
  * kernels: (1) one CTA per 128 x (512 / 2^L) tile of all 2^L slices of a
  * tube group, whose epilogue applies the inverse lift (Eq. 3) across the 2^L
  * tensor-memory accumulators, so the wavelet-domain product never reaches
  * HBM; (2) a persistent wide-tile GEMM into the wavelet-domain product, then
- * a separate inverse lift.  Both compute the same product (Algorithm 1); the
- * faster depends on the shape.  wp_wprod takes the variant stored for the
- * shape in a process-wide plan cache keyed by (n1, n2, n4, p, L, prec), else
- * a rule of thumb measured on GB300.
+ * a separate inverse lift; (3) the tile of (1) whose own producer warps
+ * apply the forward lift (Eq. 2) and the BF16 split to the spatial operands,
+ * so that W(A) and W(B) do not reach HBM either (L <= 3, n2 and n4 multiples
+ * of 4, A, B and C 16-byte aligned; elsewhere a stored variant 3 falls back
+ * to the rule for (1) and (2)).  All compute the same product (Algorithm 1);
+ * the fastest depends on the shape.  wp_wprod takes the variant stored for
+ * the shape in a process-wide plan cache keyed by (n1, n2, n4, p, L, prec),
+ * else a rule of thumb measured on GB300.
  *
- * wp_wprod_tune: times both variants on the caller's tensors (one warm-up
+ * wp_wprod_tune: times the variants on the caller's tensors (one warm-up
  * call, then the mean of three back-to-back calls each, CUDA events on
- * `stream`), stores the faster in the cache and returns it in *variant
- * (1 fused epilogue, 2 persistent GEMM + inverse lift) and its time in
- * *best_ms (if not NULL).  C holds the product on return.  Synchronises
+ * `stream`), stores the fastest in the cache and returns it in *variant
+ * (1 fused epilogue, 2 persistent GEMM + inverse lift, 3 lifted operands +
+ * fused epilogue) and its time in *best_ms (if not NULL).  C holds the product on return.  Synchronises
  * `stream`; do not call it while the stream is being captured.  For
  * arguments with a single kernel (FP32, FP8, transposes, L = 0 or L > 5) it
  * runs wp_wprod once and returns WP_OK with *variant = 0.
- * wp_plan_set: stores variant 1 or 2 for the key; <= 0 removes the entry.
+ * wp_plan_set: stores variant 1, 2 or 3 for the key; <= 0 removes the entry.
  * wp_plan_get: *variant = the cached value, 0 if none.
  * wp_plan_clear: empties the cache.
  * wp_plan_save / wp_plan_load: write / read the cache as a text file of one

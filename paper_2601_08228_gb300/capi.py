@@ -290,13 +290,14 @@ def wp_gwprod_backward(A, B, G, L, levels, prec="fp32", need_dA=True, need_dB=Tr
     return dA, dB
 
 
-WPROD_VARIANTS = {"fused": 1, "persistent": 2}
+WPROD_VARIANTS = {"fused": 1, "persistent": 2, "lifted": 3}
 
 
 def wp_wprod_tune(A, B, L, prec="bf16x3", out=None, ws=None):
-    """Time both tensor-core w-product kernels on these tensors and cache the
-    faster; returns (variant, best_ms): 1 fused inverse-lift epilogue, 2
-    persistent GEMM + inverse lift; (0, 0.0) when there is only one kernel."""
+    """Time the tensor-core w-product kernels on these tensors and cache the
+    fastest; returns (variant, best_ms): 1 fused inverse-lift epilogue, 2
+    persistent GEMM + inverse lift, 3 lift in the producer warps + inverse-lift
+    epilogue; (0, 0.0) when there is only one kernel."""
     _req(A, "A"), _req(B, "B")
     p, n1, n2, n4 = _prod_dims(A, B, False, False)
     pr = _prec(prec)

@@ -28,6 +28,10 @@
 //                         of a tube group, 2^L TMEM accumulators, inverse lift
 //                         (Eq. 3) across them in the epilogue: the fused
 //                         w-product for small slices.
+//   tc_wprod_lift_kernel  the same tile with the forward lift (Eq. 2) and the
+//                         BF16 split done by its own converter warps on the
+//                         spatial FP32 operands (L <= 3): the w-product in one
+//                         launch, nothing but A, B and C in HBM.
 // Operands are prepared by `split` kernels that round the FP32 wavelet-domain
 // slices to BF16 hi (/ lo) and, where the stored layout is not K-major,
 // transpose through shared memory, or by lift-and-split kernels that also
@@ -1026,6 +1030,290 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ---- w-product with the forward lift in the operand producer ----------------------------
+//
+// tc_wprod_lift_kernel has the tile of tc_gemm_ilift_kernel (one CTA owns a
+// 128 x BN tile of all G = 2^L wavelet-domain slices of a tube group, G TMEM
+// accumulators of BN = 512 / G columns, the inverse lift in the epilogue) but
+// reads the SPATIAL operands: for every K step of 16, converter warps load
+// the FP32 tiles of the group's G slices (A: 128 rows x 16 K; B: 16 K rows x
+// BN columns), apply the forward lift across the group in registers (Eq. 2),
+// split each value into BF16 hi + lo and store the 2G operand tiles of the
+// step into shared memory in the layouts the MMA reads: A K-major without
+// swizzle (8-row x 16-byte core matrices), B MN-major with the 128-byte
+// swizzle (the layout a TMA load of W(B) in its natural orientation gives).
+// Neither W(A), W(B) nor the wavelet-domain product reaches HBM: A and B are
+// read once from HBM (the neighbouring tiles re-read them through L2) and C
+// is written once.
+template <int L, int NPROD>
+struct LiftLayout {
+  static constexpr int G = 1 << L;
+  static constexpr int BN = 512 / G;                    // G accumulators fill the 512 TMEM columns
+  static constexpr int KS = 16;                         // K per stage: one MMA K step
+  static constexpr int NCOPY = (NPROD == 1) ? 1 : 2;
+  static constexpr int A_TILE = BM * KS * 2;            // 16 row groups x 2 core matrices of 128 B
+  static constexpr int B_TILE = BN * KS * 2;            // BN / 64 blocks of 16 K rows x 128 B
+  static constexpr int B_OFF = NCOPY * G * A_TILE;      // A tiles [copy][slice], then B tiles [copy][slice]
+  static constexpr int STAGE = NCOPY * G * (A_TILE + B_TILE);
+  static constexpr int STAGES = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
+  static constexpr int BAR_OFF = STAGES * STAGE;
+  static constexpr int SMEM = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;
+  static constexpr int CH = 64 / G < 16 ? 64 / G : 16;  // columns per epilogue chunk
+  // converter work units of one stage: A, 8 rows x 16 K; B, 2 K rows x 64
+  // columns; each unit covers all G slices (4 consecutive values per lane)
+  static constexpr int A_UNITS = BM / 8;
+  static constexpr int B_UNITS = (KS / 2) * (BN / 64);
+  static constexpr int UNITS = A_UNITS + B_UNITS;
+  static constexpr int CONV = (L == 3) ? 12 : 16;       // converter warps: UNITS / CONV units each
+  static constexpr int THREADS = 32 * (1 + CONV);
+  static constexpr int UPW = (UNITS + CONV - 1) / CONV;
+  static_assert(STAGES >= 2, "two stages at least");
+  static_assert(BN % 64 == 0 && CH >= 4, "MN-major B blocks and the TMA-store epilogue");
+};
+
+// Component c (a compile-time constant after unrolling) of a float4.
+__device__ __forceinline__ float f4_get(const float4& v, int c) {
+  return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void f4_set(float4& v, int c, float x) {
+  if (c == 0) v.x = x;
+  else if (c == 1) v.y = x;
+  else if (c == 2) v.z = x;
+  else v.w = x;
+}
+
+// hi / lo BF16 pairs of four FP32 values (hi = bf16(x), lo = bf16(x - hi)),
+// packed as they are stored: value j in bits [16 (j % 2), 16 (j % 2) + 16) of word j / 2.
+__device__ __forceinline__ void split4_bf16(const float (&x)[4], uint2& hi, uint2& lo) {
+  const __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]);
+  const __nv_bfloat162 h1 = __floats2bfloat162_rn(x[2], x[3]);
+  const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+  const __nv_bfloat162 l0 = __floats2bfloat162_rn(x[0] - f0.x, x[1] - f0.y);
+  const __nv_bfloat162 l1 = __floats2bfloat162_rn(x[2] - f1.x, x[3] - f1.y);
+  hi = make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+  lo = make_uint2(*reinterpret_cast<const uint32_t*>(&l0), *reinterpret_cast<const uint32_t*>(&l1));
+}
+
+// A (p, M, K) and B (p, K, N) spatial FP32, K % 4 == 0, N % 4 == 0, 16-byte
+// aligned; C (p, M, N) written through tmC (boxes of 32 columns x 128 rows x
+// SPP slices).  Grid (ceil(N / BN), ceil(M / 128), p / G).
+template <int L, int NPROD>
+__global__ void __launch_bounds__(LiftLayout<L, NPROD>::THREADS, 1)
+    tc_wprod_lift_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                         const __grid_constant__ CUtensorMap tmC, int M, int N, int K, int* status) {
+  using Lay = LiftLayout<L, NPROD>;
+  constexpr int G = Lay::G, BN = Lay::BN, CH = Lay::CH, STAGES = Lay::STAGES, CONV = Lay::CONV;
+  constexpr int SPP = fused_store_slices(G, BN, STAGES * Lay::STAGE);
+  static_assert(SPP >= 1, "staging room for one slice");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lay::BAR_OFF);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int64_t g = blockIdx.z;
+  const int nk = (K + Lay::KS - 1) / Lay::KS;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&full[s], CONV);    // one arrival per converter warp
+      ptx::mbar_init(&empty[s], 1);      // the MMA commit
+    }
+    ptx::mbar_init(accum, 1);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0) ptx::tmem_alloc(tmem_slot, 512);
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_bf16_f32_bmn(BM, BN);
+      for (int it = 0; it < nk && ok; ++it) {
+        const int s = it % STAGES;
+        ok = ptx::mbar_wait(&full[s], (it / STAGES) & 1, status);
+        if (!ok) break;
+        ptx::tc_fence_after();
+        const uint8_t* st = smem + s * Lay::STAGE;
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+          const uint32_t d = tmem + uint32_t(t * BN);
+          const uint64_t ah = ptx::sdesc_kmajor_noswz(st + t * Lay::A_TILE, 128, 256);
+          const uint64_t bh = ptx::sdesc_mnmajor_sw128(st + Lay::B_OFF + t * Lay::B_TILE, 2048);
+          ptx::mma_bf16(d, ah, bh, idesc, it > 0 ? 1u : 0u);
+          if constexpr (NPROD == 3) {
+            const uint64_t al = ptx::sdesc_kmajor_noswz(st + (G + t) * Lay::A_TILE, 128, 256);
+            const uint64_t bl = ptx::sdesc_mnmajor_sw128(st + Lay::B_OFF + (G + t) * Lay::B_TILE, 2048);
+            ptx::mma_bf16(d, ah, bl, idesc, 1u);
+            ptx::mma_bf16(d, al, bh, idesc, 1u);
+          }
+        }
+        ptx::mma_commit(&empty[s]);
+      }
+      ptx::mma_commit(accum);
+    }
+    __syncwarp();
+  } else {
+    const int cw = warp - 1;
+    const int64_t MK = int64_t(M) * K, KN = int64_t(K) * N;
+    const float* Ag = A + g * G * MK;
+    const float* Bg = B + g * G * KN;
+    // lane roles, fixed for the whole loop
+    const int ar = (lane & 15) >> 1;                      // A: row within the 8-row group
+    const int aq = ((lane >> 4) << 1) | (lane & 1);       // A: K quarter (4 values)
+    const int a_soff = (lane >> 4) * 128 + ar * 16 + (lane & 1) * 8;
+    const int bh = lane >> 4, bc = lane & 15;             // B: K row of the pair, 4-column group
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % STAGES, k0 = it * Lay::KS;
+      // this warp's units of the stage: loads first (no dependence on the ring)
+      float4 v[Lay::UPW][G];
+#pragma unroll
+      for (int i = 0; i < Lay::UPW; ++i) {
+        const int u = cw + i * CONV;
+        bool in = false;
+        const float* src = nullptr;
+        int64_t sstride = 0;
+        if (u < Lay::A_UNITS) {
+          const int row = m0 + 8 * u + ar, kc = k0 + 4 * aq;
+          in = row < M && kc < K;
+          src = Ag + int64_t(row) * K + kc;
+          sstride = MK;
+        } else if (u < Lay::UNITS) {
+          const int ub = u - Lay::A_UNITS, j = ub % (Lay::KS / 2), cb = ub / (Lay::KS / 2);
+          const int krow = k0 + 2 * j + bh, col = n0 + 64 * cb + 4 * bc;
+          in = krow < K && col < N;
+          src = Bg + int64_t(krow) * N + col;
+          sstride = KN;
+        }
+#pragma unroll
+        for (int t = 0; t < G; ++t)
+          v[i][t] = in ? __ldg(reinterpret_cast<const float4*>(src + t * sstride)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      if (it >= STAGES) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
+      if (!__all_sync(0xffffffffu, ok)) {
+        ok = false;
+        break;
+      }
+      uint8_t* st = smem + s * Lay::STAGE;
+#pragma unroll
+      for (int i = 0; i < Lay::UPW; ++i) {
+        const int u = cw + i * CONV;
+        if (u >= Lay::UNITS) break;
+        // forward lift across the group, one of the four values at a time
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float x[G], y[G];
+#pragma unroll
+          for (int t = 0; t < G; ++t) x[t] = f4_get(v[i][t], c);
+          lift_group<L>(x, y);
+#pragma unroll
+          for (int t = 0; t < G; ++t) f4_set(v[i][t], c, y[t]);
+        }
+        int off;
+        uint8_t* base;
+        int tile;
+        if (u < Lay::A_UNITS) {
+          off = u * 256 + a_soff;
+          base = st;
+          tile = Lay::A_TILE;
+        } else {
+          const int ub = u - Lay::A_UNITS, j = ub % (Lay::KS / 2), cb = ub / (Lay::KS / 2);
+          const int kr = 2 * j + bh;
+          off = cb * 2048 + kr * 128 + ((((bc >> 1) ^ (kr & 7))) << 4) + (bc & 1) * 8;
+          base = st + Lay::B_OFF;
+          tile = Lay::B_TILE;
+        }
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+          const float x4[4] = {v[i][t].x, v[i][t].y, v[i][t].z, v[i][t].w};
+          uint2 hi, lo;
+          split4_bf16(x4, hi, lo);
+          *reinterpret_cast<uint2*>(base + t * tile + off) = hi;
+          if constexpr (NPROD == 3) *reinterpret_cast<uint2*>(base + (G + t) * tile + off) = lo;
+        }
+      }
+      // make the stores visible to the tensor core, then one arrival per warp
+      ptx::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&full[s]);
+    }
+
+    // epilogue: the CONV warps read the G accumulators (warp & 3 selects the
+    // 32-lane quarter of TMEM), inverse-lift across them (Eq. 3), stage SPP
+    // slices at a time in the idle pipeline buffers and store them with TMA
+    constexpr int NGRP = CONV / 4;
+    const int grp = cw / 4;
+    const bool wait_ok = ptx::mbar_wait(accum, 0, status);
+    ok = ok && wait_ok;
+    ptx::tc_fence_after();
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    const uint32_t lane_base = tmem + (uint32_t(quad * 32) << 16);
+    const bool leader = (warp == 1 && lane == 0);
+    auto epi_sync = [] { asm volatile("bar.sync 1, %0;" ::"n"(Lay::CONV * 32) : "memory"); };
+#pragma unroll
+    for (int pass = 0; pass < G / SPP; ++pass) {
+      if (pass > 0) {
+        if (leader) ptx::bulk_wait_read_all();
+        epi_sync();
+      }
+      if (ok) {
+#pragma unroll 1
+        for (int c0 = grp * CH; c0 < BN; c0 += NGRP * CH) {
+          if (n0 + c0 >= N) break;
+          uint32_t raw[G * CH];
+#pragma unroll
+          for (int t = 0; t < G; ++t) ptx::tmem_ld_cols_async<CH>(lane_base + uint32_t(t * BN + c0), raw + t * CH);
+          ptx::tmem_wait_regs<G * CH>(raw);
+          const int h = c0 / 32, q0 = (c0 % 32) / 4;
+#pragma unroll
+          for (int j = 0; j < CH; j += 4) {
+            float xs[SPP][4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              float y[G], x[G];
+#pragma unroll
+              for (int t = 0; t < G; ++t) y[t] = __uint_as_float(raw[t * CH + j + jj]);
+              ilift_group<L>(y, x);
+#pragma unroll
+              for (int tt = 0; tt < SPP; ++tt) xs[tt][jj] = x[pass * SPP + tt];
+            }
+#pragma unroll
+            for (int tt = 0; tt < SPP; ++tt) {
+              uint8_t* rowp = smem + (h * SPP + tt) * 16384 + r * 128;
+              *reinterpret_cast<float4*>(rowp + (((q0 + j / 4) ^ (r & 7)) << 4)) =
+                  make_float4(xs[tt][0], xs[tt][1], xs[tt][2], xs[tt][3]);
+            }
+          }
+        }
+      }
+      ptx::fence_proxy_async_smem();
+      epi_sync();
+      if (leader && ok) {
+#pragma unroll
+        for (int h = 0; h < BN / 32; ++h)
+          if (n0 + 32 * h < N) ptx::tma_store_3d(&tmC, smem + h * SPP * 16384, n0 + 32 * h, m0, int(g * G + pass * SPP));
+        ptx::bulk_commit();
+      }
+    }
+    if (leader) ptx::bulk_wait_all();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    if (!ok) ptx::mbar_wait(accum, 0, nullptr, 100000000ull);
+    __syncwarp();
+    ptx::tmem_dealloc(tmem, 512);
+  }
+}
+
 }  // namespace tc
 
 // ---- host side -------------------------------------------------------------------------
@@ -1332,6 +1620,26 @@ static int launch_fused(const CUtensorMap& ah, const CUtensorMap& al, const CUte
   return launch_status();
 }
 
+// The lifted-operand kernel: no workspace, no preparation launch.
+template <int L, int NPROD>
+static int launch_lift(const float* A, const float* B, float* C, int64_t M, int64_t N, int64_t K, int64_t p,
+                       cudaStream_t st) {
+  using Lay = tc::LiftLayout<L, NPROD>;
+  auto kern = tc::tc_wprod_lift_kernel<L, NPROD>;
+  static bool attr = false;
+  if (!attr) {
+    WP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM));
+    attr = true;
+  }
+  constexpr int SPP = tc::fused_store_slices(Lay::G, Lay::BN, Lay::STAGES * Lay::STAGE);
+  CUtensorMap mc;
+  WP_TRY(make_map_f32(&mc, C, N, M, p, 32, tc::BM, SPP));
+  const dim3 grid(unsigned((N + Lay::BN - 1) / Lay::BN), unsigned((M + tc::BM - 1) / tc::BM), unsigned(p >> L));
+  WP_PROFILE(NPROD == 3 ? "tc_wprod_lift_bf16x3" : "tc_wprod_lift_bf16", st);
+  kern<<<grid, Lay::THREADS, Lay::SMEM, st>>>(A, B, mc, int(M), int(N), int(K), device_status_ptr());
+  return launch_status();
+}
+
 template <int L>
 static int fused_levels(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
                         bool x3, __nv_bfloat16* Ah, __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl,
@@ -1487,6 +1795,30 @@ bool wprod_tunable(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int pre
   return (prec == WP_PREC_BF16 || prec == WP_PREC_BF16X3) && fused_domain(n1, n2, n4, p, L, prec);
 }
 
+// Arguments the lifted-operand kernel takes: L <= 3 (all 2^L slices of a
+// K step in one shared-memory stage), rows of A and B in whole float4s,
+// 16-byte aligned A, B and C (C is written by TMA stores).
+bool wprod_lift_ok(const float* A, const float* B, const float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
+                   int L, int prec) {
+  return wprod_tunable(n1, n2, n4, p, L, prec) && L <= 3 && n2 % 4 == 0 && n4 % 4 == 0 && aligned16(A) &&
+         aligned16(B) && aligned16(C) && (n1 + tc::BM - 1) / tc::BM <= 65535;
+}
+
+// Whether wp_wprod takes the lifted-operand kernel: the tuned variant if
+// there is one for the shape, else at L <= 2 with at most two column tiles
+// of 512 / 2^L (each column tile converts the whole row band of A again).
+// Measured on GB300, BF16x3: 192 x 256^3 62 / 70 / 91 us at L = 1 / 2 / 3
+// against 82 / 78 / 82 us for the best of the other two kernels; 64 x 1024 x
+// 256 x 512 at L = 2 (four column tiles) 126 us against 113 us (fused).
+static bool use_lift(const float* A, const float* B, const float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
+                     int L, int prec) {
+  if (!wprod_lift_ok(A, B, C, n1, n2, n4, p, L, prec)) return false;
+  const int v = wprod_plan_lookup(n1, n2, n4, p, L, prec);
+  if (v != 0) return v == kVariantLifted;
+  const int64_t bn = 512 >> L;
+  return L <= 2 && (n4 + bn - 1) / bn <= 2;
+}
+
 // C = A *w B for tensor-core precisions with the transform fused into the
 // operand preparation and the GEMM epilogue.  WP_ERR_UNSUPPORTED when the
 // arguments fall outside the fused path (the caller then uses the unfused one).
@@ -1504,8 +1836,15 @@ int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t
       default: return wprod_fp8_levels<5>(A, B, C, n1, n2, n4, p, ws, ws_bytes, st);
     }
   }
-  const int64_t Kp = pad8(n2);
   const bool x3 = (prec == WP_PREC_BF16X3);
+  if (use_lift(A, B, C, n1, n2, n4, p, L, prec)) {
+    switch (L) {
+      case 1: return x3 ? launch_lift<1, 3>(A, B, C, n1, n4, n2, p, st) : launch_lift<1, 1>(A, B, C, n1, n4, n2, p, st);
+      case 2: return x3 ? launch_lift<2, 3>(A, B, C, n1, n4, n2, p, st) : launch_lift<2, 1>(A, B, C, n1, n4, n2, p, st);
+      default: return x3 ? launch_lift<3, 3>(A, B, C, n1, n4, n2, p, st) : launch_lift<3, 1>(A, B, C, n1, n4, n2, p, st);
+    }
+  }
+  const int64_t Kp = pad8(n2);
   const bool epilogue_fused = use_epilogue_fused(n1, n2, n4, p, L, prec);
   Carver cv(ws, ws_bytes);
   float* Chat = epilogue_fused ? nullptr : cv.take<float>(size_t(p) * n1 * n4);

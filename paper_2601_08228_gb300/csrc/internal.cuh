@@ -33,7 +33,12 @@ int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t
 // from for these arguments: the fused inverse-lift epilogue kernel, or the
 // persistent GEMM into C_hat plus a separate inverse lift.
 bool wprod_tunable(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec);
-constexpr int kVariantFused = 1, kVariantPersistent = 2;
+// True when the third kernel, which lifts the spatial operands in its
+// producer warps (L <= 3, n2 and n4 multiples of 4, 16-byte aligned A, B, C),
+// takes these arguments.
+bool wprod_lift_ok(const float* A, const float* B, const float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
+                   int L, int prec);
+constexpr int kVariantFused = 1, kVariantPersistent = 2, kVariantLifted = 3;
 // The tuned variant for this shape (tune.cu); 0 if none.
 int wprod_plan_lookup(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec);
 

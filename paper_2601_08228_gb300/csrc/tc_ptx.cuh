@@ -145,6 +145,20 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(const void* smem_tile) {
   return d;
 }
 
+// Shared-memory matrix descriptor: K-major operand tile without swizzle, built
+// from 8-row x 16-byte core matrices (each 128 contiguous bytes); core
+// matrices adjacent in K are `k_bytes` apart (leading byte offset), 8-row
+// groups `mn_bytes` apart (stride byte offset).
+__device__ __forceinline__ uint64_t sdesc_kmajor_noswz(const void* smem_tile, uint32_t k_bytes, uint32_t mn_bytes) {
+  const uint64_t addr = smem_u32(smem_tile);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;                       // start address (16-byte units)
+  d |= uint64_t((k_bytes >> 4) & 0x3FFF) << 16;       // leading byte offset: next core matrix in K
+  d |= uint64_t((mn_bytes >> 4) & 0x3FFF) << 32;      // stride byte offset: next 8 rows
+  d |= uint64_t(1) << 46;                             // descriptor version for tcgen05
+  return d;                                           // layout 0: no swizzle
+}
+
 // Shared-memory matrix descriptor: MN-major operand tile stored as 128-byte
 // rows along MN (64 BF16) with consecutive rows consecutive in K, 128-byte
 // swizzle; 8-row K groups 1024 bytes apart (stride byte offset), 64-element

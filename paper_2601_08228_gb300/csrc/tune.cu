@@ -1,12 +1,14 @@
 // Autotuner and plan cache of the tensor-core w-product.
 //
-// The BF16 / BF16x3 w-product (gemm_tc.cu) has two kernels: one that keeps
+// The BF16 / BF16x3 w-product (gemm_tc.cu) has three kernels: one that keeps
 // all 2^L wavelet-domain accumulators of a tile in tensor memory and applies
-// the inverse lift in its epilogue (narrow tiles, no C_hat round trip), and
-// a persistent wide-tile GEMM into C_hat followed by a separate inverse lift.
+// the inverse lift in its epilogue (narrow tiles, no C_hat round trip), the
+// same tile with the forward lift done by its own producer warps on the
+// spatial operands (L <= 3: no W(A), W(B) round trip either), and a
+// persistent wide-tile GEMM into C_hat followed by a separate inverse lift.
 // Which is faster depends on the shape (tile width against 512 / 2^L, K,
-// the number of tiles against the SM count), so wp_wprod_tune times both on
-// the caller's tensors and keeps the faster in a process-wide cache keyed by
+// the number of tiles against the SM count), so wp_wprod_tune times them on
+// the caller's tensors and keeps the fastest in a process-wide cache keyed by
 // (n1, n2, n4, p, L, precision); wp_wprod consults it before its rule of
 // thumb.  The cache can be written to and read from a text file of one JSON
 // object per line.
@@ -26,7 +28,7 @@ namespace wp {
 
 using PlanKey = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int>;
 struct PlanVal {
-  int variant;          // kVariantFused or kVariantPersistent
+  int variant;          // kVariantFused, kVariantPersistent or kVariantLifted
   double ms;
 };
 
@@ -44,7 +46,7 @@ static void plan_store(const PlanKey& k, int variant, double ms) {
   g_plans[k] = PlanVal{variant, ms};
 }
 
-static bool valid_variant(int v) { return v == kVariantFused || v == kVariantPersistent; }
+static bool valid_variant(int v) { return v == kVariantFused || v == kVariantPersistent || v == kVariantLifted; }
 
 static bool plan_erase(const PlanKey& k, PlanVal* old) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -162,8 +164,10 @@ extern "C" int wp_wprod_tune(const float* A, const float* B, float* C, int64_t n
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WP_ERR_CUDA;
   int best = 0;
   float best_t = 0.f;
-  for (int v : {kVariantFused, kVariantPersistent}) {
+  const bool lift = wprod_lift_ok(A, B, C, n1, n2, n4, p, L, prec);
+  for (int v : {kVariantFused, kVariantPersistent, kVariantLifted}) {
     if (rc != WP_OK) break;
+    if (v == kVariantLifted && !lift) continue;
     plan_store(key, v, -1.0);
     // one warm-up call, then the mean of three back-to-back calls
     rc = wp_wprod(A, B, C, n1, n2, n4, p, L, 0, 0, prec, ws, ws_bytes, stream);

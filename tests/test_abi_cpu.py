@@ -98,7 +98,7 @@ def test_plan_cache_round_trip(libwprod, tmp_path):
     assert capi.wp_plan_get(256, 256, 256, 192, 3, "bf16x3") == 2
     assert capi.wp_plan_get(256, 256, 256, 192, 3, "bf16") == 0          # another key
     with pytest.raises(capi.WPError) as e:
-        capi.wp_plan_set(256, 256, 256, 192, 3, "bf16x3", 3)               # no such variant
+        capi.wp_plan_set(256, 256, 256, 192, 3, "bf16x3", 4)               # no such variant
     assert e.value.status == capi.WP_ERR_SHAPE
     with pytest.raises(capi.WPError) as e:
         capi.wp_plan_set(256, 256, 256, 12, 3, "bf16x3", 1)               # p % 2^L

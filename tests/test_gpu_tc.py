@@ -261,13 +261,50 @@ def test_wprod_both_kernels(p, n1, n2, n4, L, variant, prec):
     assert capi.wp_get_device_error() == 0
 
 
+LIFT_CASES = [
+    # p, n1, n2, n4, L: shapes the lifted-operand kernel takes (n2, n4 multiples of 4)
+    (96, 256, 256, 256, 3),     # the benchmark's slice shape
+    (48, 200, 100, 260, 3),     # ragged rows, K % 16 == 4, columns beyond the last 64-block
+    (16, 130, 36, 516, 2),
+    (8, 64, 40, 256, 1),
+    (8, 1, 4, 4, 3),            # one row, one K quarter, one column group
+    (16, 300, 64, 128, 2),
+]
+
+
+@pytest.mark.parametrize("p,n1,n2,n4,L", LIFT_CASES)
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_wprod_lifted_kernel(p, n1, n2, n4, L, prec):
+    """The kernel that lifts the spatial operands in its producer warps gives
+    the w-product (against the FP64 oracle) and the same product as the
+    fused-epilogue kernel fed by the separate lift-and-split pass."""
+    A, B = rand((p, n1, n2), 25), rand((p, n2, n4), 26)
+    Ad, Bd = dev(A), dev(B)
+    capi.wp_plan_clear()
+    try:
+        capi.wp_plan_set(n1, n2, n4, p, L, prec, "lifted")
+        capi.wp_profile_begin()
+        C = host(capi.wp_wprod(Ad, Bd, L, prec=prec))
+        prof = capi.wp_profile_end()
+        capi.wp_plan_set(n1, n2, n4, p, L, prec, "fused")
+        Cf = host(capi.wp_wprod(Ad, Bd, L, prec=prec))
+    finally:
+        capi.wp_plan_clear()
+    assert any(k.startswith("tc_wprod_lift") for k in prof), prof
+    err = O.rel_fro(C, O.wprod(A, B, L))
+    assert err <= (TOL_X3 if prec == "bf16x3" else TOL_BF16), err
+    # same BF16 operands and the same MMA sequence per 16-wide K step
+    assert O.rel_fro(C, Cf) <= 1e-6
+    assert capi.wp_get_device_error() == 0
+
+
 def test_wprod_tuner():
     p, n1, n2, n4, L = 64, 256, 192, 256, 3
     A, B = rand((p, n1, n2), 23), rand((p, n2, n4), 24)
     Ad, Bd = dev(A), dev(B)
     capi.wp_plan_clear()
     v, ms = capi.wp_wprod_tune(Ad, Bd, L, prec="bf16x3")
-    assert v in (1, 2) and ms > 0
+    assert v in (1, 2, 3) and ms > 0
     assert capi.wp_plan_get(n1, n2, n4, p, L, "bf16x3") == v
     C = host(capi.wp_wprod(Ad, Bd, L, prec="bf16x3"))
     assert O.rel_fro(C, O.wprod(A, B, L)) <= TOL_X3

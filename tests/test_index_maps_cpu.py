@@ -328,3 +328,141 @@ def test_panel4_qr_restatement(m, n):
     assert np.allclose(np.tril(R, -1), 0)
     np.testing.assert_allclose(np.abs(R), np.abs(np.linalg.qr(X, mode="r")), atol=1e-9)
     np.testing.assert_allclose(R.T @ R, X.T @ X, atol=1e-8)
+
+
+# ---- tc_wprod_lift_kernel: converter-warp maps onto the MMA operand layouts ----------
+
+def _lift_layout(L, nprod):
+    G = 1 << L
+    BN = 512 // G
+    ncopy = 1 if nprod == 1 else 2
+    a_tile, b_tile = 128 * 16 * 2, BN * 16 * 2
+    stage = ncopy * G * (a_tile + b_tile)
+    conv = 12 if L == 3 else 16
+    a_units, b_units = 128 // 8, 8 * (BN // 64)
+    return dict(G=G, BN=BN, a_tile=a_tile, b_tile=b_tile, b_off=ncopy * G * a_tile, stage=stage,
+                stages=min(8, 196608 // stage), conv=conv, a_units=a_units, units=a_units + b_units,
+                upw=cdiv(a_units + b_units, conv))
+
+
+def _lift_stage_writes(L, M, N, K, m0, n0, k0, nprod=3):
+    """Every 8-byte shared-memory store of one K step of one CTA, restated from
+    the kernel: (warp, lane, slice t, copy, byte offset in the stage,
+    global element coordinates of the 4 values or None for zero fill)."""
+    lay = _lift_layout(L, nprod)
+    G, BN = lay["G"], lay["BN"]
+    out = []
+    for cw in range(lay["conv"]):
+        for i in range(lay["upw"]):
+            u = cw + i * lay["conv"]
+            if u >= lay["units"]:
+                break
+            for lane in range(32):
+                if u < lay["a_units"]:
+                    ar, aq = (lane & 15) >> 1, ((lane >> 4) << 1) | (lane & 1)
+                    row, kc = m0 + 8 * u + ar, k0 + 4 * aq
+                    src = ("A", row, kc) if (row < M and kc < K) else None
+                    off = u * 256 + (lane >> 4) * 128 + ar * 16 + (lane & 1) * 8
+                    base, tile = 0, lay["a_tile"]
+                    elem = ("A", 8 * u + ar, 4 * aq)          # (row, k) within the tile
+                else:
+                    ub = u - lay["a_units"]
+                    j, cb = ub % 8, ub // 8
+                    bh, bc = lane >> 4, lane & 15
+                    krow, col = k0 + 2 * j + bh, n0 + 64 * cb + 4 * bc
+                    src = ("B", krow, col) if (krow < K and col < N) else None
+                    kr = 2 * j + bh
+                    off = cb * 2048 + kr * 128 + (((bc >> 1) ^ (kr & 7)) << 4) + (bc & 1) * 8
+                    base, tile = lay["b_off"], lay["b_tile"]
+                    elem = ("B", kr, 64 * cb + 4 * bc)        # (k, column) within the tile
+                for t in range(G):
+                    for copy in range(1 if nprod == 1 else 2):
+                        out.append((cw, lane, t, copy, base + (copy * G + t) * tile + off, src, elem))
+    return lay, out
+
+
+def _a_canonical(r, k):
+    """K-major, no swizzle: 8-row x 16-byte core matrices, K neighbours 128 B
+    apart (leading byte offset), 8-row groups 256 B apart (stride byte offset)."""
+    return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2
+
+
+def _b_canonical(k, n):
+    """MN-major, 128-byte swizzle, 16 K rows per 64-column block (blocks 2 KB
+    apart): row k of block n // 64 at 128 k, 16-byte chunk (n % 64) / 8 XOR k % 8."""
+    return (n // 64) * 2048 + k * 128 + ((((n % 64) >> 3) ^ (k & 7)) << 4) + (n & 7) * 2
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_lift_kernel_stage_layout(L):
+    """One K step: every (row, k) of the 2G A tiles and every (k, column) of the
+    2G B tiles is written exactly once, at the address the MMA descriptors read
+    (the canonical layouts above), inside the stage; the stage ring, the
+    epilogue staging and the barriers fit the shared memory."""
+    lay, writes = _lift_stage_writes(L, 4096, 4096, 4096, 0, 0, 0)
+    G, BN = lay["G"], lay["BN"]
+    seen = {}
+    for cw, lane, t, copy, addr, src, elem in writes:
+        assert 0 <= addr and addr + 8 <= lay["stage"]
+        kind, a, b = elem
+        for v in range(4):
+            if kind == "A":
+                exp = (copy * G + t) * lay["a_tile"] + _a_canonical(a, b + v)
+            else:
+                exp = lay["b_off"] + (copy * G + t) * lay["b_tile"] + _b_canonical(a, b + v)
+            assert addr + 2 * v == exp
+            assert exp not in seen
+            seen[exp] = (kind, t, copy, a, b + v)
+    # all bytes of the stage written once (2 bytes per value)
+    assert len(seen) * 2 == lay["stage"]
+    # tile bases: 1024-byte aligned for the swizzled B tiles
+    assert lay["b_off"] % 1024 == 0 and lay["b_tile"] % 1024 == 0 and lay["stage"] % 1024 == 0
+    spp = G
+    while spp > 0 and spp * 128 * BN * 4 > lay["stages"] * lay["stage"]:
+        spp >>= 1
+    assert spp >= 1
+    smem = lay["stages"] * lay["stage"] + (2 * lay["stages"] + 1) * 8 + 16 + 1024
+    assert smem <= 232448
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_lift_kernel_stage_stores_conflict_free(L):
+    """The 8-byte stores of each half-warp fill 128 distinct bytes of one
+    128-byte line set (no bank conflicts)."""
+    lay, writes = _lift_stage_writes(L, 4096, 4096, 4096, 0, 0, 0)
+    # one store instruction per (warp, unit, slice, copy); a half-warp's 16
+    # lanes are served together and their 8-byte stores must touch 32
+    # distinct banks
+    per = {}
+    for cw, lane, t, copy, addr, src, elem in writes:
+        unit = (elem[0], elem[1] // 8) if elem[0] == "A" else (elem[0], elem[1] // 2, elem[2] // 64)
+        key = (cw, unit, t, copy, lane >> 4)
+        per.setdefault(key, []).extend([(addr // 4) % 32, (addr // 4 + 1) % 32])
+    for key, banks in per.items():
+        assert len(banks) == 32 and len(set(banks)) == 32, key
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 260, 100), (1, 4, 4), (130, 516, 36), (256, 256, 256)])
+@pytest.mark.parametrize("L", [1, 3])
+def test_lift_kernel_loads_in_bounds(L, M, N, K):
+    """Every load of every K step of every tile stays inside the operand
+    (K % 4 == 0, N % 4 == 0; rows, columns and K beyond the edges read as
+    zero), and together the loads cover each element of A and B."""
+    lay = _lift_layout(L, 3)
+    BN = lay["BN"]
+    seen_a, seen_b = set(), set()
+    for n0 in range(0, N, BN):
+        for m0 in range(0, M, 128):
+            for k0 in range(0, K, 16):
+                _, writes = _lift_stage_writes(L, M, N, K, m0, n0, k0)
+                for cw, lane, t, copy, addr, src, elem in writes:
+                    if src is None or t or copy:
+                        continue
+                    kind, a, b = src
+                    if kind == "A":
+                        assert 0 <= a < M and 0 <= b and b + 4 <= K
+                        seen_a.update((a, b + v) for v in range(4))
+                    else:
+                        assert 0 <= a < K and 0 <= b and b + 4 <= N
+                        seen_b.update((a, b + v) for v in range(4))
+    assert len(seen_a) == M * K and len(seen_b) == K * N
