@@ -499,6 +499,38 @@ def _ws(capi, w, L, prec):
     return _WS_CACHE[key]
 
 
+def _wprod_kernels(capi, reps=10):
+    """ms per call and TFLOP/s of each tensor-core w-product kernel (1 fused
+    inverse-lift epilogue, 2 persistent GEMM + inverse lift, 3 lifted operands
+    + fused epilogue) on the benchmark's A, B at L = 1, 2, 3, and the kernel
+    wp_wprod picks by its rule."""
+    import torch
+    w = WORKLOAD
+    A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
+    C = torch.empty((w["p"], w["n1"], w["n4"]), device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for L in (1, 2, 3):
+        ws = torch.empty(capi.wp_wprod_workspace(w["n1"], w["n2"], w["n4"], w["p"], L, "bf16x3"),
+                         dtype=torch.uint8, device="cuda")
+        row = {}
+        for v in ("fused", "persistent", "lifted", None):
+            capi.wp_plan_clear()
+            if v:
+                capi.wp_plan_set(w["n1"], w["n2"], w["n4"], w["p"], L, "bf16x3", v)
+            fn = lambda: capi.wp_wprod(A, B, L, prec="bf16x3", out=C, ws=ws)
+            t = _time_loop(fn, flush, 3, reps) / reps
+            row[v or "rule"] = {"ms": t * 1e3, "tflops": wprod_flops() / t / 1e12}
+        capi.wp_plan_clear()
+        capi.wp_profile_begin()
+        capi.wp_wprod(A, B, L, prec="bf16x3", out=C, ws=ws)
+        names = capi.wp_profile_end()
+        row["rule_picks"] = ("lifted" if any(k.startswith("tc_wprod_lift") for k in names) else
+                             "fused" if any(k.startswith("tc_gemm_ilift") for k in names) else "persistent")
+        res[f"L{L}"] = row
+    return res
+
+
 def _time_loop(fn, flush, warmup, steps):
     import torch
     for _ in range(warmup):
@@ -755,6 +787,9 @@ def _extras(capi, args):
     capi.wp_set_jacobi_column_split(True)
     out["jacobi_kernels"] = ker
     del Aw
+    # the three BF16x3 w-product kernels at the benchmark's slice shape for
+    # L = 1, 2, 3 (forced through the plan cache; L2 flushed before each call)
+    out["wprod_kernels"] = _wprod_kernels(capi)
     # deblurring step at 512 x 512 x 128, L = 4
     n, p, L = 512, 128, 4
     K = synth.blur_operator(n, p, dtype=np.float32)
