@@ -1071,6 +1071,17 @@ struct LiftLayout {
   static_assert(BN % 64 == 0 && CH >= 4, "MN-major B blocks and the TMA-store epilogue");
 };
 
+// 16-byte read-only load that does not allocate in L1 and has L2 fetch the
+// whole 128-byte line (the converter warps read each line in two halves, one
+// K step apart, long after L1 would have evicted it).
+__device__ __forceinline__ float4 ldg_stream4(const float* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::128B.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
 // Component c (a compile-time constant after unrolling) of a float4.
 __device__ __forceinline__ float f4_get(const float4& v, int c) {
   return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
@@ -1193,7 +1204,7 @@ __global__ void __launch_bounds__(LiftLayout<L, NPROD>::THREADS, 1)
         }
 #pragma unroll
         for (int t = 0; t < G; ++t)
-          v[i][t] = in ? __ldg(reinterpret_cast<const float4*>(src + t * sstride)) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[i][t] = in ? ldg_stream4(src + t * sstride) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       if (it >= STAGES) ok = ptx::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status);
       if (!__all_sync(0xffffffffu, ok)) {
@@ -1807,9 +1818,9 @@ bool wprod_lift_ok(const float* A, const float* B, const float* C, int64_t n1, i
 // Whether wp_wprod takes the lifted-operand kernel: the tuned variant if
 // there is one for the shape, else at L <= 2 with at most two column tiles
 // of 512 / 2^L (each column tile converts the whole row band of A again).
-// Measured on GB300, BF16x3: 192 x 256^3 62 / 70 / 91 us at L = 1 / 2 / 3
-// against 82 / 78 / 82 us for the best of the other two kernels; 64 x 1024 x
-// 256 x 512 at L = 2 (four column tiles) 126 us against 113 us (fused).
+// Measured on GB300, BF16x3: 192 x 256^3 60 / 69 / 91 us at L = 1 / 2 / 3
+// against 82 / 78 / 81 us for the best of the other two kernels; 64 x 1024 x
+// 256 x 512 at L = 2 (four column tiles) 128 us against 113 us (fused).
 static bool use_lift(const float* A, const float* B, const float* C, int64_t n1, int64_t n2, int64_t n4, int64_t p,
                      int L, int prec) {
   if (!wprod_lift_ok(A, B, C, n1, n2, n4, p, L, prec)) return false;
