@@ -57,7 +57,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-launch and deblurring measurements")
     ap.add_argument("--profile-case", choices=["lift", "gemm", "gemm_large", "sgemm", "wprod", "wprod_fp8", "jacobi", "jacobi_row_split",
-                                               "batched", "glift", "jacobi_global", "wprod_fused", "wprod_lift", "lift_inverse"],
+                                               "batched", "glift", "jacobi_global", "wprod_fused", "wprod_lift", "wprod_lift_L1",
+                                               "lift_inverse"],
                     default=None,
                     help="run one small invocation of one kernel (for ncu captures) and exit")
     return ap.parse_args()
@@ -982,12 +983,14 @@ def run_profile_case(case):
         w = WORKLOAD
         capi.wp_plan_set(w["n1"], w["n2"], w["n4"], w["p"], w["L"], "bf16x3", "fused")
         capi.wp_wprod(A, B, w["L"], prec="bf16x3")
-    elif case == "wprod_lift":
-        # the kernel that lifts the spatial operands in its producer warps, at the benchmark's shape
+    elif case in ("wprod_lift", "wprod_lift_L1"):
+        # the kernel that lifts the spatial operands in its producer warps, at the benchmark's
+        # shape (L = 3, forced) or at L = 1 (where the dispatch rule picks it)
         A, B = (torch.from_numpy(x).cuda() for x in inputs(np.float32))
         w = WORKLOAD
-        capi.wp_plan_set(w["n1"], w["n2"], w["n4"], w["p"], w["L"], "bf16x3", "lifted")
-        capi.wp_wprod(A, B, w["L"], prec="bf16x3")
+        L = w["L"] if case == "wprod_lift" else 1
+        capi.wp_plan_set(w["n1"], w["n2"], w["n4"], w["p"], L, "bf16x3", "lifted")
+        capi.wp_wprod(A, B, L, prec="bf16x3")
     elif case == "lift_inverse":
         # exported Mallat-order inverse at L = 4: 256 slices of 1024 x 512 (537 MB in)
         y = torch.rand((256, 1024, 512), device="cuda")
