@@ -222,7 +222,11 @@ WP_API int wp_facewise(const float* Ah, const float* Bh, float* Ch, int64_t n1, 
 /* ---- a1 + a2 + a4: the w-product (Def. 2.1, Algorithm 1) ---------------- */
 
 /* C = op(A) *w op(B) = W^{-1}( W(op A) Delta W(op B) ), op as in
- * wp_facewise; C is (p, n1, n4) spatial. */
+ * wp_facewise; C is (p, n1, n4) spatial.  BF16 / BF16X3 without transposes
+ * run one of the three tensor-core w-product kernels described with the
+ * plan cache below (the stored variant, else a rule of thumb); the size
+ * wp_wprod_workspace returns covers all of them (the kernel that lifts the
+ * operands in its producer warps uses none). */
 WP_API int wp_wprod_workspace(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec,
                        size_t* bytes);
 WP_API int wp_wprod(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
