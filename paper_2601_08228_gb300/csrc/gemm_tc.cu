@@ -1775,7 +1775,8 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
   return lift_dispatch(LIFT_INV, Chat, C, n1 * n4, p, L, st, true);
 }
 
-// Which of the two BF16 / BF16x3 w-product kernels a shape takes.  The
+// Which of the fused-epilogue and persistent BF16 / BF16x3 w-product kernels
+// a shape takes when the lifted-operand kernel does not (lift_variant).  The
 // inverse-lift epilogue needs all 2^L accumulators of a tile in TMEM, so its
 // tile is only 512 / 2^L wide.  Rule of thumb, measured on GB300 (BF16x3,
 // the 256 x 256 x 192 L = 3 case and neighbours): the fused kernel wins with
@@ -1783,7 +1784,8 @@ static int wprod_fp8_levels(const float* A, const float* B, float* C, int64_t n1
 // of C dominates) and small slices (n1, n4 <= 128); otherwise the persistent
 // wide-tile GEMM into C_hat plus a separate inverse lift is faster (88 vs
 // 96 us at 256 x 256 x 192).  A choice timed by wp_wprod_tune for the shape
-// (plan cache, tune.cu) takes precedence: 1 fused, 2 persistent + inverse lift.
+// (plan cache, tune.cu) takes precedence: 1 fused, 2 persistent + inverse
+// lift, 3 lifted operands + fused epilogue.
 static bool fused_rule(int64_t n1, int64_t n2, int64_t n4, int L) {
   const int64_t bn_fused = 512 >> L;
   return (n4 + bn_fused - 1) / bn_fused <= 4 && (L <= 2 || n2 <= 64 || (n1 <= 128 && n4 <= 128));

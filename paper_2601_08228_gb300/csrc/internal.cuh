@@ -29,9 +29,10 @@ int tc_facewise(const float* A, const float* B, float* C, int64_t M, int64_t N, 
 // WP_ERR_UNSUPPORTED outside its domain (no transposes, 1 <= L <= 5).
 int tc_wprod_fused(const float* A, const float* B, float* C, int64_t n1, int64_t n2, int64_t n4,
                    int64_t p, int L, int prec, void* ws, size_t ws_bytes, cudaStream_t st);
-// True when wp_wprod (no transposes) has two tensor-core kernels to choose
-// from for these arguments: the fused inverse-lift epilogue kernel, or the
-// persistent GEMM into C_hat plus a separate inverse lift.
+// True when wp_wprod (no transposes) has several tensor-core kernels to
+// choose from for these arguments: the fused inverse-lift epilogue kernel,
+// the persistent GEMM into C_hat plus a separate inverse lift, and (where
+// wprod_lift_ok also holds) the lifted-operand kernel.
 bool wprod_tunable(int64_t n1, int64_t n2, int64_t n4, int64_t p, int L, int prec);
 // True when the third kernel, which lifts the spatial operands in its
 // producer warps (L <= 3, n2 and n4 multiples of 4, 16-byte aligned A, B, C),
