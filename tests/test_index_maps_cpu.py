@@ -466,3 +466,39 @@ def test_lift_kernel_loads_in_bounds(L, M, N, K):
                         assert 0 <= a < K and 0 <= b and b + 4 <= N
                         seen_b.update((a, b + v) for v in range(4))
     assert len(seen_a) == M * K and len(seen_b) == K * N
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_lift_kernel_epilogue_covers_tile_once(L):
+    """Epilogue of tc_wprod_lift_kernel: the converter warps (TMEM lane
+    quarter = warp & 3, column group = converter index // 4) cover every
+    (row, column) of the 128 x BN tile exactly once per store pass, and the
+    staged float4s of a pass (SPP slices, 32-column blocks of 128-byte rows,
+    128-byte swizzle) land at distinct addresses inside the pipeline buffers."""
+    lay = _lift_layout(L, 3)
+    G, BN = lay["G"], lay["BN"]
+    CH = min(64 // G, 16)
+    conv, first = lay["conv"], 1
+    ngrp = conv // 4
+    spp = G
+    while spp > 0 and spp * 128 * BN * 4 > lay["stages"] * lay["stage"]:
+        spp >>= 1
+    seen, addrs = set(), set()
+    for cw in range(conv):
+        warp = cw + first
+        quad, grp = warp & 3, cw // 4
+        for lane in range(32):
+            r = quad * 32 + lane
+            for c0 in range(grp * CH, BN, ngrp * CH):
+                h, q0 = c0 // 32, (c0 % 32) // 4
+                for j in range(0, CH, 4):
+                    for tt in range(spp):
+                        a = (h * spp + tt) * 16384 + r * 128 + (((q0 + j // 4) ^ (r & 7)) << 4)
+                        assert 0 <= a and a + 16 <= lay["stages"] * lay["stage"]
+                        assert a not in addrs
+                        addrs.add(a)
+                    for jj in range(4):
+                        key = (r, c0 + j + jj)
+                        assert key not in seen
+                        seen.add(key)
+    assert len(seen) == 128 * BN
